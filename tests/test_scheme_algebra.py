@@ -1,0 +1,89 @@
+"""The paper's scheme algebra (Sec. 2.3-4) pinned against its own Table of
+operation and barrier counts (Sec. 5), its identity S_U T_P = N_{P,U}
+(Sec. 3.2), and against the separable oracle on images."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import scheme_algebra as sa
+
+
+def wavelets():
+    a, b, g, d, K, _ = oracle.cdf97_constants()
+    return {"CDF 5/3": (sa.cdf53(), 1.0, 1.0, oracle.CDF53),
+            "CDF 9/7": (sa.cdf97(a, b, g, d), 1.0 / K, K, oracle.CDF97),
+            "DD 13/7": (sa.dd137(), 1.0, 1.0, oracle.DD137)}
+
+
+def test_operation_and_barrier_table(golden):
+    rows = golden("op_barrier_counts.txt")
+    assert len(rows) == 30
+    W = wavelets()
+    for wname, scheme, barriers, ops in rows:
+        pairs = W[wname][0]
+        assert sa.barrier_count(scheme, len(pairs)) == int(barriers), (wname, scheme)
+        assert sa.op_count(scheme, pairs) == int(ops), (wname, scheme)
+
+
+def _eq(a, b, tol):
+    return all(a[i][j].close(b[i][j], tol) for i in range(4) for j in range(4))
+
+
+@pytest.mark.parametrize("wname", ["CDF 5/3", "CDF 9/7", "DD 13/7"])
+def test_monolithic_product_is_polyphase(wname):
+    pairs, _, _, _ = wavelets()[wname]
+    tol = 0 if wname != "CDF 9/7" else 1e-13
+    for p, u in pairs:
+        assert _eq(sa.matmul(sa.S_M(u), sa.T_M(p)), sa.N_PU(p, u), tol)
+
+
+@pytest.mark.parametrize("wname", ["CDF 5/3", "CDF 9/7", "DD 13/7"])
+@pytest.mark.parametrize("scheme", [s for s in sa.SCHEMES if s != "Convolution"])
+def test_every_scheme_equals_separable(wname, scheme):
+    pairs, _, _, _ = wavelets()[wname]
+    tol = 0 if wname != "CDF 9/7" else 1e-12
+    assert _eq(sa.product(sa.scheme_matrices(scheme, pairs)), sa.full_matrix(pairs), tol)
+
+
+def test_the_counts_are_not_vacuous():
+    # a dropped term or a wrong sign changes a count or breaks the identity
+    p, u = sa.cdf53()[0]
+    bad = sa.with_entries({(sa.HL, sa.LL): sa.horiz(p), (sa.LH, sa.LL): sa.vert(p),
+                           (sa.HH, sa.HL): sa.vert(p), (sa.HH, sa.LH): sa.horiz(p)})
+    assert not _eq(sa.matmul(sa.S_M(u), bad), sa.N_PU(p, u), 0)
+    flipped = sa.with_entries({(sa.HL, sa.LL): sa.horiz(p), (sa.LH, sa.LL): sa.vert(p),
+                               (sa.HH, sa.LL): -(sa.horiz(p) * sa.vert(p)),
+                               (sa.HH, sa.HL): sa.vert(p), (sa.HH, sa.LH): sa.horiz(p)})
+    assert not _eq(sa.matmul(sa.S_M(u), flipped), sa.N_PU(p, u), 0)
+
+
+def _ext_components(x, E):
+    """Polyphase components of the WSS-extended image, E quads of margin."""
+    h, w = x.shape
+    H2 = 2 * ((h + 1) // 2 + 2 * E)
+    W2 = 2 * ((w + 1) // 2 + 2 * E)
+    rows = [oracle.mirror(r - 2 * E, h) for r in range(H2)]
+    cols = [oracle.mirror(c - 2 * E, w) for c in range(W2)]
+    xe = x[np.ix_(rows, cols)]
+    return [xe[0::2, 0::2], xe[0::2, 1::2], xe[1::2, 0::2], xe[1::2, 1::2]]
+
+
+@pytest.mark.parametrize("wname", ["CDF 5/3", "CDF 9/7", "DD 13/7"])
+@pytest.mark.parametrize("scheme", [s for s in sa.SCHEMES if s != "Convolution"])
+@pytest.mark.parametrize("h,w", [(12, 14), (9, 11)])
+def test_scheme_steps_on_image_match_oracle(wname, scheme, h, w):
+    pairs, slo, shi, wid = wavelets()[wname]
+    x = np.random.default_rng(h * 100 + w).integers(0, 256, (h, w)).astype(float)
+    E = 8
+    comps = _ext_components(x, E)
+    for m in sa.scheme_matrices(scheme, pairs):
+        comps = sa.apply_matrix(m, comps, E)
+    scale = (slo * slo, slo * shi, shi * slo, shi * shi)
+    ch, cw = (h + 1) // 2, (w + 1) // 2
+    fh, fw = h // 2, w // 2
+    ref = oracle.dwt2(x, wid, 1)
+    crop = [c[E:E + ch, E:E + cw] * s for c, s in zip(comps, scale)]
+    assert np.abs(crop[0] - ref[:ch, :cw]).max() < 1e-9
+    assert np.abs(crop[1][:, :fw] - ref[:ch, cw:]).max() < 1e-9
+    assert np.abs(crop[2][:fh, :] - ref[ch:, :cw]).max() < 1e-9
+    assert np.abs(crop[3][:fh, :fw] - ref[ch:, cw:]).max() < 1e-9
