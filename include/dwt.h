@@ -1,0 +1,182 @@
+/*
+ * libdwt -- multi-level 2-D discrete wavelet transform on one GB300 GPU.
+ *
+ * The transform is the one stated in the paper (Barina, Kula, Zemcik,
+ * "Parallel Wavelet Schemes for Images"): an image is split into its four
+ * polyphase components (LL, HL, LH, HH; Sec. 2.3) and mapped by a chain of
+ * 2-D lifting steps (Sec. 2.4-4) built from the 1-D predict/update pairs of
+ * the wavelet (Sec. 2.2, Sec. 5).  Every scheme (separable, single-loop,
+ * Iwahashi, Explosive, Monolithic, Polyphase, their starred variants and
+ * Convolution) computes the same coefficients up to rounding (Sec. 7).
+ *
+ * Conventions shared by every entry point:
+ *   - Images are row-major 2-D planes with a row pitch in BYTES.  Device
+ *     pointers must be CUDA device (or managed) memory; host pointers are
+ *     rejected with DWT_EINVAL, never dereferenced on the GPU.
+ *   - Output layout (forward) / input layout (inverse): Mallat packing of a
+ *     w x h plane.  At level k the level's input is W_k x H_k (W_0 = w,
+ *     W_{k+1} = ceil(W_k / 2)); its LL band is ceil(W_k/2) x ceil(H_k/2) at
+ *     the top-left, HL (horizontal high-pass) at the top-right, LH at the
+ *     bottom-left and HH at the bottom-right; level k+1 recurses into LL.
+ *   - Boundary: whole-sample symmetric extension; a dimension of length 1
+ *     is left untouched.  Even samples are low-pass (JPEG 2000 origin).
+ *   - Normalisation (default): JPEG 2000, i.e. low-pass DC gain 1 and
+ *     high-pass Nyquist gain 2 (5/3 unscaled; 9/7 low x 1/K, high x K).
+ *   - All calls that take a stream are asynchronous with respect to the
+ *     host; errors detected on the host are returned as dwt_status and
+ *     never abort or throw across the ABI.  Device-side failures (a bounded
+ *     wait that ran out) are reported through dwt_plan_device_status() or a
+ *     batch's status array.
+ *   - The transform is out-of-place: input and output must not overlap.
+ *   - A plan owns its scratch memory; one plan must not be in flight on two
+ *     streams at once (use one plan per concurrent slot).
+ *
+ * All functions are thread-safe for distinct plans.
+ */
+#ifndef LIBDWT_DWT_H
+#define LIBDWT_DWT_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same type as cudaStream_t; NULL is the legacy default stream. */
+typedef struct CUstream_st* dwt_stream;
+
+typedef struct dwt_plan_s* dwt_plan;
+
+typedef enum {
+  DWT_OK = 0,
+  DWT_EINVAL = 1,       /* bad argument: size, level count, pitch, pointer, aliasing */
+  DWT_ENOMEM = 2,       /* device or host allocation failed */
+  DWT_EUNSUPPORTED = 3, /* valid but not provided (e.g. 9/7 with int32) */
+  DWT_ECUDA = 4,        /* a CUDA runtime call failed */
+  DWT_ETIMEOUT = 5,     /* a bounded device-side wait gave up */
+  DWT_EBUSY = 6         /* a resource is in use (e.g. one plan twice in a batch) */
+} dwt_status;
+
+typedef enum {
+  DWT_CDF53 = 0, /* P = -1/2 (1 + z^-1), U = 1/4 (1 + z) (Sec. 5)                  */
+  DWT_CDF97 = 1, /* two pairs (alpha, beta), (gamma, delta) (Sec. 5)              */
+  DWT_DD137 = 2  /* Deslauriers-Dubuc (4,4): degree-3 P and U (Sec. 5)            */
+} dwt_wavelet;
+
+typedef enum {
+  DWT_F32 = 0,  /* float32 storage and arithmetic                                    */
+  DWT_F16S = 1, /* float16 storage, float32 arithmetic                              */
+  DWT_I32 = 2   /* int32, reversible 5/3 with JPEG 2000 floor rounding, bit-exact    */
+} dwt_dtype;
+
+typedef enum {
+  DWT_AUTO = 0,        /* chosen by the autotuner (persisted cache)                 */
+  DWT_ROWCOL = 1,      /* separable, all columns then all rows through global memory */
+  DWT_SWELDENS = 2,    /* separable single-loop: T^H_P | T^V_P | S^H_U | S^V_U (Sec. 2.4) */
+  DWT_IWAHASHI = 3,    /* T^I_P | R^I_{P,U} | S^I_U (Sec. 2.5)                       */
+  DWT_IWAHASHI_S = 4,  /* Iwahashi* (Sec. 4)                                        */
+  DWT_EXPLOSIVE = 5,   /* T^E_P | R^E_{P,U} | S^E_U (Sec. 3.1)                      */
+  DWT_EXPLOSIVE_S = 6, /* Explosive* (Sec. 4)                                       */
+  DWT_MONOLITHIC = 7,  /* T_P | S_U (Sec. 3.2)                                      */
+  DWT_MONOLITHIC_S = 8,/* Monolithic* (Sec. 4)                                      */
+  DWT_POLYPHASE = 9,   /* N_{P,U} (Sec. 2.3)                                        */
+  DWT_POLYPHASE_S = 10,/* Polyphase* (Sec. 4)                                       */
+  DWT_CONVOLUTION = 11 /* four 2-D FIR filters with subsampling (Sec. 2.3)          */
+} dwt_scheme;
+
+typedef enum { DWT_NORM_JPEG2000 = 0, DWT_NORM_ZETA = 1 } dwt_norm;
+
+/* Create a plan for a w x h image, `levels` levels (0 = plain copy), wavelet
+ * and storage type.  Allocates the plan's device scratch (about w*h/4
+ * elements for the LL ping-pong).  Errors: DWT_EINVAL for w < 1, h < 1,
+ * levels < 0, levels above the number of halvings until both dimensions
+ * are 1, or out == NULL; DWT_EUNSUPPORTED for DWT_I32 with a wavelet other
+ * than 5/3; DWT_ENOMEM; DWT_ECUDA. */
+dwt_status dwt_plan_create(int w, int h, dwt_wavelet wavelet, int levels, dwt_dtype dtype,
+                           dwt_plan* out);
+
+/* Select the lifting scheme (default DWT_AUTO).  DWT_I32 supports
+ * DWT_ROWCOL and DWT_SWELDENS (the JPEG 2000 step order with floors is not
+ * shared by the non-separable schemes): other schemes give
+ * DWT_EUNSUPPORTED.  DWT_ROWCOL allocates a w x h intermediate plane. */
+dwt_status dwt_plan_set_scheme(dwt_plan plan, dwt_scheme scheme);
+
+/* The scheme a call will actually run (DWT_AUTO resolved). */
+dwt_status dwt_plan_get_scheme(dwt_plan plan, dwt_scheme* scheme);
+
+/* Float paths only: DWT_NORM_ZETA applies the paper's scaling step (low-pass
+ * x zeta, high-pass x 1/zeta per axis; zeta = sqrt(2) for 5/3, Sec. 5). */
+dwt_status dwt_plan_set_normalization(dwt_plan plan, dwt_norm norm);
+
+/* Forward transform.  d_in: w x h samples, d_out: w x h Mallat-packed
+ * coefficients, both device memory of the plan's dtype, pitches in bytes
+ * (>= w * element size, multiple of the element size).  The input is
+ * read-only.  Asynchronous on `stream`. */
+dwt_status dwt2_forward(dwt_plan plan, const void* d_in, size_t in_pitch_bytes, void* d_out,
+                        size_t out_pitch_bytes, dwt_stream stream);
+
+/* Inverse transform: Mallat-packed coefficients in, samples out. */
+dwt_status dwt2_inverse(dwt_plan plan, const void* d_coef, size_t coef_pitch_bytes, void* d_out,
+                        size_t out_pitch_bytes, dwt_stream stream);
+
+/* Same transforms with HOST buffers: the call copies the input to device
+ * staging owned by the plan, transforms it, and copies the result back into
+ * h_out, all on `stream`.  h_in / h_out should be page-locked for the
+ * copies to overlap; pageable memory works but synchronises.  The host
+ * output is valid after the stream is synchronised. */
+dwt_status dwt2_forward_host(dwt_plan plan, const void* h_in, size_t in_pitch_bytes, void* h_out,
+                             size_t out_pitch_bytes, dwt_stream stream);
+dwt_status dwt2_inverse_host(dwt_plan plan, const void* h_coef, size_t coef_pitch_bytes,
+                             void* h_out, size_t out_pitch_bytes, dwt_stream stream);
+
+/* Many transforms in one persistent launch.  Each request names a plan, its
+ * device buffers and a direction; different sizes, level counts, wavelets
+ * and dtypes may be mixed.  The kernel pulls (image, level, strip) work
+ * items from a global queue; a level's strips wait, with a bounded spin,
+ * for the previous level of the same image.  d_status (device memory, n
+ * ints, may be NULL) receives per request DWT_OK or DWT_ETIMEOUT.  A plan
+ * may appear at most once per call (DWT_EBUSY otherwise). */
+typedef struct {
+  dwt_plan plan;
+  const void* in;
+  size_t in_pitch;
+  void* out;
+  size_t out_pitch;
+  int inverse;
+} dwt_request;
+
+dwt_status dwt_batch_submit(const dwt_request* reqs, int n, dwt_stream stream, int* d_status);
+
+/* Synchronise with the plan's last stream and report device-side failures
+ * of its calls since the previous query (DWT_OK or DWT_ETIMEOUT). */
+dwt_status dwt_plan_device_status(dwt_plan plan);
+
+/* Per-kernel timing of a plan's calls, for measurement.  When enabled, each
+ * launch is bracketed by CUDA events on the launching stream; reading the
+ * profile synchronises on them.  Slot names are "<pass>/L<level>". */
+typedef struct {
+  char name[32];
+  int launches;
+  double total_ms;
+  double algorithmic_bytes; /* bytes the launch must move, summed over launches */
+} dwt_kernel_stat;
+
+dwt_status dwt_plan_set_profiling(dwt_plan plan, int enable);
+dwt_status dwt_plan_read_profile(dwt_plan plan, dwt_kernel_stat* stats, int capacity, int* count);
+
+/* Run the autotuner for this plan now (device memory for a trial image is
+ * allocated and freed), persisting the choice to the cache file named by
+ * the environment variable DWT_AUTOTUNE_CACHE (if set). */
+dwt_status dwt_plan_autotune(dwt_plan plan, dwt_stream stream);
+
+dwt_status dwt_plan_destroy(dwt_plan plan);
+
+const char* dwt_status_string(dwt_status status);
+
+/* Library version "major.minor.patch". */
+const char* dwt_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LIBDWT_DWT_H */

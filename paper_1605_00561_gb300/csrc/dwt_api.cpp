@@ -1,0 +1,943 @@
+// The C ABI of libdwt (include/dwt.h): plans, argument validation, the
+// per-level launch sequence, TMA descriptors, lifting coefficients,
+// Convolution taps, profiling, host-buffer entry points, batches and the
+// autotuner.  Every step of the transform runs in the CUDA kernels of this
+// library; this file only prepares and orders launches.
+#include "dwt.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "dwt_internal.h"
+
+using namespace dwt;
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// Wavelets (Sec. 5)
+// ---------------------------------------------------------------------------
+
+// CDF 9/7 lifting constants and the DC gain K of the unscaled low-pass; the
+// paper defers them to its reference [Daubechies1998] (Sec. 5).
+constexpr double kAlpha = -1.586134342059924;
+constexpr double kBeta = -0.052980118572961;
+constexpr double kGamma = 0.882911075530934;
+constexpr double kDelta = 0.443506852043971;
+constexpr double kK97 = 1.230174104914001;
+
+struct Lifting {
+  int npairs;
+  double p1[2], p3[2], u1[2], u3[2];  // taps at sample distance 1 and 3
+  double dc;                          // DC gain of the unscaled analysis low-pass
+};
+
+Lifting lifting_of(int wl) {
+  Lifting L{};
+  if (wl == DWT_CDF53) {  // P = -1/2 (1 + z^-1), U = 1/4 (1 + z)
+    L.npairs = 1;
+    L.p1[0] = -0.5;
+    L.u1[0] = 0.25;
+    L.dc = 1.0;
+  } else if (wl == DWT_CDF97) {
+    L.npairs = 2;
+    L.p1[0] = kAlpha;
+    L.u1[0] = kBeta;
+    L.p1[1] = kGamma;
+    L.u1[1] = kDelta;
+    L.dc = kK97;
+  } else {  // DD 13/7: P = 1/16 (z + z^-2) - 9/16 (1 + z^-1), U = 9/32 (1 + z) - 1/32 (z^-1 + z^2)
+    L.npairs = 1;
+    L.p1[0] = -9.0 / 16.0;
+    L.p3[0] = 1.0 / 16.0;
+    L.u1[0] = 9.0 / 32.0;
+    L.u3[0] = -1.0 / 32.0;
+    L.dc = 1.0;
+  }
+  return L;
+}
+
+// Band scaling: JPEG 2000 (low DC gain 1, high Nyquist gain 2) or the
+// paper's zeta (low x zeta, high x 1/zeta, zeta = sqrt(2)/K; sqrt(2) for 5/3).
+void band_scales(const Lifting& L, int norm, double* lo, double* hi) {
+  if (norm == DWT_NORM_ZETA) {
+    *lo = std::sqrt(2.0) / L.dc;
+    *hi = L.dc / std::sqrt(2.0);
+  } else {
+    *lo = 1.0 / L.dc;
+    *hi = L.dc;
+  }
+}
+
+// Coefficients of one launch.  A length-1 axis gets zero lifting
+// coefficients and unit scaling: the line is left as it is.
+Coefs make_coefs(const Lifting& L, int norm, int Wk, int Hk, int pass, bool inverse) {
+  Coefs c{};
+  const bool h_on = Wk > 1, v_on = Hk > 1;
+  for (int k = 0; k < L.npairs; ++k) {
+    c.ph1[k] = h_on ? (float)L.p1[k] : 0.f;
+    c.ph3[k] = h_on ? (float)L.p3[k] : 0.f;
+    c.uh1[k] = h_on ? (float)L.u1[k] : 0.f;
+    c.uh3[k] = h_on ? (float)L.u3[k] : 0.f;
+    c.pv1[k] = v_on ? (float)L.p1[k] : 0.f;
+    c.pv3[k] = v_on ? (float)L.p3[k] : 0.f;
+    c.uv1[k] = v_on ? (float)L.u1[k] : 0.f;
+    c.uv3[k] = v_on ? (float)L.u3[k] : 0.f;
+  }
+  double lo, hi;
+  band_scales(L, norm, &lo, &hi);
+  const double lo_h = h_on ? lo : 1.0, hi_h = h_on ? hi : 1.0;
+  const double lo_v = v_on ? lo : 1.0, hi_v = v_on ? hi : 1.0;
+  double s[4];
+  if (pass == PASS_VERT) {
+    s[0] = s[1] = lo_v;
+    s[2] = s[3] = hi_v;
+  } else if (pass == PASS_HORZ) {
+    s[0] = s[2] = lo_h;
+    s[1] = s[3] = hi_h;
+  } else {
+    s[0] = lo_v * lo_h;
+    s[1] = lo_v * hi_h;
+    s[2] = hi_v * lo_h;
+    s[3] = hi_v * hi_h;
+  }
+  for (int i = 0; i < 4; ++i) c.scale[i] = (float)(inverse ? 1.0 / s[i] : s[i]);
+  c.h_on = h_on;
+  c.v_on = v_on;
+  return c;
+}
+
+// 1-D polyphase matrix of the whole factorisation, as Laurent polynomials in
+// the quad offset (index + 4 covers offsets -4..4).
+struct Poly {
+  double c[9] = {0};
+};
+Poly pmul(const Poly& a, const Poly& b) {
+  Poly r;
+  for (int i = 0; i < 9; ++i)
+    for (int j = 0; j < 9; ++j) {
+      const int k = i + j - 4;
+      if (a.c[i] != 0 && b.c[j] != 0 && k >= 0 && k < 9) r.c[k] += a.c[i] * b.c[j];
+    }
+  return r;
+}
+void padd(Poly& a, const Poly& b, double s) {
+  for (int i = 0; i < 9; ++i) a.c[i] += s * b.c[i];
+}
+
+// Predict P (reads even quads at offsets 0, +1 and, degree 3, -1, +2) and
+// update U (odd quads at -1, 0 and -2, +1).
+Poly pred_poly(const Lifting& L, int k) {
+  Poly p;
+  p.c[4] = p.c[5] = L.p1[k];
+  p.c[3] = p.c[6] = L.p3[k];
+  return p;
+}
+Poly upd_poly(const Lifting& L, int k) {
+  Poly u;
+  u.c[3] = u.c[4] = L.u1[k];
+  u.c[2] = u.c[5] = L.u3[k];
+  return u;
+}
+
+// m[out][in]: forward (L,H) <- (even,odd); inverse (even,odd) <- (L,H).
+void polyphase_1d(const Lifting& L, int norm, bool on, bool inverse, Poly m[2][2]) {
+  for (int i = 0; i < 2; ++i)
+    for (int j = 0; j < 2; ++j) m[i][j] = Poly();
+  double lo, hi;
+  band_scales(L, norm, &lo, &hi);
+  if (!on) {
+    m[0][0].c[4] = m[1][1].c[4] = 1.0;
+    return;
+  }
+  if (!inverse) {
+    m[0][0].c[4] = m[1][1].c[4] = 1.0;
+    for (int k = 0; k < L.npairs; ++k) {
+      const Poly P = pred_poly(L, k), U = upd_poly(L, k);
+      for (int j = 0; j < 2; ++j) padd(m[1][j], pmul(P, m[0][j]), 1.0);  // H += P L
+      for (int j = 0; j < 2; ++j) padd(m[0][j], pmul(U, m[1][j]), 1.0);  // L += U H
+    }
+    for (int j = 0; j < 2; ++j)
+      for (int i = 0; i < 9; ++i) {
+        m[0][j].c[i] *= lo;
+        m[1][j].c[i] *= hi;
+      }
+  } else {
+    m[0][0].c[4] = 1.0 / lo;
+    m[1][1].c[4] = 1.0 / hi;
+    for (int k = L.npairs - 1; k >= 0; --k) {
+      const Poly P = pred_poly(L, k), U = upd_poly(L, k);
+      for (int j = 0; j < 2; ++j) padd(m[0][j], pmul(U, m[1][j]), -1.0);  // even -= U odd
+      for (int j = 0; j < 2; ++j) padd(m[1][j], pmul(P, m[0][j]), -1.0);  // odd -= P even
+    }
+  }
+}
+
+bool conv_taps(const Lifting& L, int norm, int Wk, int Hk, bool inverse, ConvTaps* t) {
+  Poly v[2][2], h[2][2];
+  polyphase_1d(L, norm, Hk > 1, inverse, v);
+  polyphase_1d(L, norm, Wk > 1, inverse, h);
+  for (int a = 0; a < 2; ++a)
+    for (int b = 0; b < 2; ++b)
+      for (int i = 0; i < 9; ++i)
+        if ((i < 2 || i > 6) && (std::fabs(v[a][b].c[i]) > 1e-12 || std::fabs(h[a][b].c[i]) > 1e-12))
+          return false;  // reach beyond the kernel's two quads
+  for (int so = 0; so < 2; ++so)
+    for (int sx = 0; sx < 2; ++sx)
+      for (int ti = 0; ti < 2; ++ti)
+        for (int tx = 0; tx < 2; ++tx)
+          for (int dy = 0; dy < 5; ++dy)
+            for (int dx = 0; dx < 5; ++dx)
+              t->t[so][sx][ti][tx][dy][dx] = (float)(v[so][ti].c[dy + 2] * h[sx][tx].c[dx + 2]);
+  return true;
+}
+
+// ---------------------------------------------------------------------------
+// Kernel lookup, geometry, TMA
+// ---------------------------------------------------------------------------
+const GroupFn kGroups[] = {group_sweldens, group_iwahashi, group_explosive, group_monolithic,
+                           group_polyphase, group_convolution, group_rowcol};
+
+bool find_kernel(const LaunchKey& k, int ns, KernelInfo* info) {
+  for (GroupFn g : kGroups) {
+    cudaError_t e = cudaSuccess;
+    if (g(k, ns, info, nullptr, &e)) return true;
+  }
+  return false;
+}
+
+cudaError_t call_kernel(const LaunchKey& k, int ns, const LaunchCall& call) {
+  for (GroupFn g : kGroups) {
+    cudaError_t e = cudaSuccess;
+    if (g(k, ns, nullptr, &call, &e)) return e;
+  }
+  return cudaErrorInvalidDeviceFunction;
+}
+
+struct Occ {
+  int sms = 0;
+  int per_sm = 0;
+};
+std::mutex g_occ_mu;
+std::map<std::pair<const void*, int>, Occ> g_occ;
+
+Occ occupancy(const KernelInfo& ki, int device) {
+  std::lock_guard<std::mutex> lk(g_occ_mu);
+  auto key = std::make_pair(ki.fn, device);
+  auto it = g_occ.find(key);
+  if (it != g_occ.end()) return it->second;
+  Occ o;
+  cudaDeviceGetAttribute(&o.sms, cudaDevAttrMultiProcessorCount, device);
+  int optin = 0;
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+  cudaFuncSetAttribute(ki.fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       optin > 0 ? optin : (int)ki.smem_bytes);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o.per_sm, ki.fn, kWarpsPerCta * 32,
+                                                    ki.smem_bytes) != cudaSuccess)
+    o.per_sm = 1;
+  o.sms = std::max(o.sms, 1);
+  o.per_sm = std::max(o.per_sm, 1);
+  g_occ[key] = o;
+  return o;
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+typedef CUresult (*AddrRangeFn)(CUdeviceptr*, size_t*, CUdeviceptr);
+
+template <class F>
+F driver_fn(const char* name) {
+  void* p = nullptr;
+  cudaDriverEntryPointQueryResult q;
+  if (cudaGetDriverEntryPointByVersion(name, &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+      q != cudaDriverEntryPointSuccess)
+    return nullptr;
+  return reinterpret_cast<F>(p);
+}
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = driver_fn<EncodeTiledFn>("cuTensorMapEncodeTiled");
+  return fn;
+}
+AddrRangeFn addr_range_fn() {
+  static AddrRangeFn fn = driver_fn<AddrRangeFn>("cuMemGetAddressRange");
+  return fn;
+}
+
+bool encode_2d(CUtensorMap* m, int dtype, const void* base, int w, int h, size_t pitch_bytes,
+               int boxw, int boxh) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn || w < 1 || h < 1 || (reinterpret_cast<uintptr_t>(base) & 15) || (pitch_bytes & 15))
+    return false;
+  const CUtensorMapDataType dt = dtype == F32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                 : dtype == F16S ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                                 : CU_TENSOR_MAP_DATA_TYPE_INT32;
+  cuuint64_t dims[2] = {(cuuint64_t)w, (cuuint64_t)h};
+  cuuint64_t strides[1] = {(cuuint64_t)pitch_bytes};
+  cuuint32_t box[2] = {(cuuint32_t)boxw, (cuuint32_t)boxh};
+  cuuint32_t estr[2] = {1, 1};
+  return fn(m, dt, 2, const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+size_t elem_size(int dtype) { return dtype == F16S ? 2 : 4; }
+
+size_t round_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Plans
+// ---------------------------------------------------------------------------
+struct ProfSlot {
+  std::string name;
+  int launches = 0;
+  double ms = 0, bytes = 0;
+};
+struct ProfRec {
+  int slot;
+  cudaEvent_t a, b;
+  double bytes;
+};
+
+struct dwt_plan_s {
+  int w = 0, h = 0, levels = 0, wavelet = 0, dtype = 0;
+  int scheme = DWT_AUTO, auto_scheme = -1, norm = DWT_NORM_JPEG2000;
+  int device = 0;
+  size_t es = 4;
+  std::vector<int> W, H;
+  void* scratch[2] = {nullptr, nullptr};
+  size_t scratch_pitch = 0;
+  void* tmp = nullptr;
+  size_t tmp_pitch = 0;
+  void* stage_in = nullptr;
+  void* stage_out = nullptr;
+  size_t stage_pitch = 0;
+  int* d_status = nullptr;
+  cudaStream_t last_stream = nullptr;
+  bool profiling = false;
+  std::vector<ProfSlot> slots;
+  std::vector<ProfRec> pending;
+  std::vector<cudaEvent_t> pool;
+  int nstages = 4;
+  int tmin = 8;
+  std::mutex mu;
+};
+
+namespace {
+
+dwt_status from_cuda(cudaError_t e) {
+  if (e == cudaSuccess) return DWT_OK;
+  if (e == cudaErrorMemoryAllocation) return DWT_ENOMEM;
+  return DWT_ECUDA;
+}
+
+// ---- autotune cache (text lines "key scheme") ----------------------------
+std::mutex g_cache_mu;
+
+std::string gpu_name(int device) {
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) return "unknown";
+  std::string s = prop.name;
+  for (char& c : s)
+    if (c == ' ') c = '_';
+  return s;
+}
+
+std::string cache_key(const dwt_plan_s* p) {
+  char buf[256];
+  std::snprintf(buf, sizeof buf, "%s|wl%d|dt%d|%dx%d|L%d", gpu_name(p->device).c_str(), p->wavelet,
+                p->dtype, p->w, p->h, p->levels);
+  return buf;
+}
+
+int cache_lookup(const std::string& key) {
+  const char* path = std::getenv("DWT_AUTOTUNE_CACHE");
+  if (!path) return -1;
+  std::lock_guard<std::mutex> lk(g_cache_mu);
+  FILE* f = std::fopen(path, "r");
+  if (!f) return -1;
+  char k[256];
+  int v, found = -1;
+  while (std::fscanf(f, "%255s %d", k, &v) == 2)
+    if (key == k) found = v;
+  std::fclose(f);
+  return found;
+}
+
+void cache_store(const std::string& key, int scheme) {
+  const char* path = std::getenv("DWT_AUTOTUNE_CACHE");
+  if (!path) return;
+  std::lock_guard<std::mutex> lk(g_cache_mu);
+  FILE* f = std::fopen(path, "a");
+  if (!f) return;
+  std::fprintf(f, "%s %d\n", key.c_str(), scheme);
+  std::fclose(f);
+}
+
+int default_scheme(const dwt_plan_s* p) {
+  return p->dtype == DWT_I32 ? DWT_SWELDENS : DWT_MONOLITHIC_S;
+}
+
+bool scheme_supported(int wavelet, int dtype, int scheme) {
+  if (scheme <= DWT_AUTO || scheme >= NUM_SCHEMES) return false;
+  if (wavelet == DWT_DD137) return false;
+  if (dtype == DWT_I32) return wavelet == DWT_CDF53 && (scheme == DWT_ROWCOL || scheme == DWT_SWELDENS);
+  return true;
+}
+
+int resolve_scheme(dwt_plan_s* p) {
+  if (p->scheme != DWT_AUTO) return p->scheme;
+  if (p->auto_scheme < 0) {
+    int s = cache_lookup(cache_key(p));
+    p->auto_scheme = scheme_supported(p->wavelet, p->dtype, s) ? s : default_scheme(p);
+  }
+  return p->auto_scheme;
+}
+
+bool device_pointer_ok(const void* ptr, size_t extent, int device) {
+  if (!ptr) return false;
+  cudaPointerAttributes attr;
+  if (cudaPointerGetAttributes(&attr, ptr) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  if (attr.type == cudaMemoryTypeDevice) {
+    if (attr.device != device) return false;
+  } else if (attr.type != cudaMemoryTypeManaged) {
+    return false;
+  }
+  if (AddrRangeFn fn = addr_range_fn()) {
+    CUdeviceptr base = 0;
+    size_t size = 0;
+    if (fn(&base, &size, reinterpret_cast<CUdeviceptr>(ptr)) == CUDA_SUCCESS) {
+      const uintptr_t lo = reinterpret_cast<uintptr_t>(ptr);
+      if (lo + extent > (uintptr_t)base + size) return false;
+    }
+  }
+  return true;
+}
+
+size_t plane_extent(int w, int h, size_t pitch, size_t es) {
+  return (size_t)(h - 1) * pitch + (size_t)w * es;
+}
+
+bool overlaps(const void* a, size_t na, const void* b, size_t nb) {
+  const uintptr_t x = reinterpret_cast<uintptr_t>(a), y = reinterpret_cast<uintptr_t>(b);
+  return x < y + nb && y < x + na;
+}
+
+cudaEvent_t take_event(dwt_plan_s* p) {
+  if (!p->pool.empty()) {
+    cudaEvent_t e = p->pool.back();
+    p->pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+int slot_of(dwt_plan_s* p, const std::string& name) {
+  for (size_t i = 0; i < p->slots.size(); ++i)
+    if (p->slots[i].name == name) return (int)i;
+  p->slots.push_back(ProfSlot{name});
+  return (int)p->slots.size() - 1;
+}
+
+// One launch: geometry, descriptors, optional timing events.
+dwt_status launch(dwt_plan_s* p, const LaunchKey& key, LevelArgs& a, const Coefs& cf,
+                  const ConvTaps& ct, cudaStream_t s, const char* slot) {
+  KernelInfo ki{};
+  if (!find_kernel(key, p->nstages, &ki)) return DWT_EUNSUPPORTED;
+  const Occ oc = occupancy(ki, p->device);
+  const int cap = oc.sms * oc.per_sm;
+  a.ncs = (a.cw + ki.uq - 1) / ki.uq;
+  const int ctas_row = (a.ncs + kWarpsPerCta - 1) / kWarpsPerCta;
+  const int nrs_target = std::max(1, cap / ctas_row);
+  a.T = std::max(p->tmin, (a.ch + nrs_target - 1) / nrs_target);
+  a.nrs = (a.ch + a.T - 1) / a.T;
+  a.nstages = p->nstages;
+  a.status = p->d_status;
+
+  TmaMaps maps;
+  std::memset(&maps, 0, sizeof maps);
+  a.src_tma = 0;
+  if (a.W >= 2 && a.H >= 2) {
+    const size_t es = p->es;
+    if (ki.load == SAMPLES) {
+      a.src_tma = encode_2d(&maps.m[0], p->dtype, a.src[0], a.W, a.H, (size_t)a.src_pitch[0] * es,
+                            ki.box_w, ki.box_h);
+    } else {
+      const int pw[4] = {a.cw, a.fw, a.cw, a.fw}, ph[4] = {a.ch, a.ch, a.fh, a.fh};
+      bool ok = true;
+      for (int i = 0; i < 4 && ok; ++i)
+        ok = encode_2d(&maps.m[i], p->dtype, a.src[i], pw[i], ph[i], (size_t)a.src_pitch[i] * es,
+                       ki.box_w, ki.box_h);
+      a.src_tma = ok;
+    }
+  }
+
+  ProfRec rec{-1, nullptr, nullptr, 0.0};
+  if (p->profiling) {
+    rec.slot = slot_of(p, slot);
+    rec.a = take_event(p);
+    rec.b = take_event(p);
+    rec.bytes = 2.0 * a.W * (double)a.H * p->es;
+    cudaEventRecord(rec.a, s);
+  }
+  LaunchCall call{&a, &maps, &cf, &ct, s};
+  cudaError_t e = call_kernel(key, p->nstages, call);
+  if (p->profiling) {
+    cudaEventRecord(rec.b, s);
+    p->pending.push_back(rec);
+  }
+  return from_cuda(e);
+}
+
+void level_dims(const dwt_plan_s* p, int k, LevelArgs& a) {
+  a.W = p->W[k];
+  a.H = p->H[k];
+  a.cw = (a.W + 1) / 2;
+  a.ch = (a.H + 1) / 2;
+  a.fw = a.W / 2;
+  a.fh = a.H / 2;
+}
+
+dwt_status ensure_tmp(dwt_plan_s* p) {
+  if (p->tmp) return DWT_OK;
+  p->tmp_pitch = round_up((size_t)p->w * p->es, 128);
+  return from_cuda(cudaMalloc(&p->tmp, p->tmp_pitch * p->h));
+}
+
+// The transform proper: levels in order (forward) or reverse (inverse).
+dwt_status run(dwt_plan_s* p, bool inverse, const void* src, size_t src_pitch, void* dst,
+               size_t dst_pitch, cudaStream_t s) {
+  const size_t es = p->es;
+  if (src_pitch < (size_t)p->w * es || dst_pitch < (size_t)p->w * es || src_pitch % es ||
+      dst_pitch % es)
+    return DWT_EINVAL;
+  const size_t nsrc = plane_extent(p->w, p->h, src_pitch, es);
+  const size_t ndst = plane_extent(p->w, p->h, dst_pitch, es);
+  if (!device_pointer_ok(src, nsrc, p->device) || !device_pointer_ok(dst, ndst, p->device))
+    return DWT_EINVAL;
+  if (overlaps(src, nsrc, dst, ndst)) return DWT_EINVAL;
+  int cur = -1;
+  if (cudaGetDevice(&cur) != cudaSuccess || cur != p->device) return DWT_EINVAL;
+  p->last_stream = s;
+  if (p->levels == 0)
+    return from_cuda(cudaMemcpy2DAsync(dst, dst_pitch, src, src_pitch, (size_t)p->w * es, p->h,
+                                       cudaMemcpyDeviceToDevice, s));
+  const int scheme = resolve_scheme(p);
+  if (!scheme_supported(p->wavelet, p->dtype, scheme)) return DWT_EUNSUPPORTED;
+  if (scheme == DWT_ROWCOL) {
+    dwt_status st = ensure_tmp(p);
+    if (st != DWT_OK) return st;
+  }
+  const Lifting L = lifting_of(p->wavelet);
+  const int Lv = p->levels;
+  char slot[32];
+  for (int step = 0; step < Lv; ++step) {
+    const int k = inverse ? Lv - 1 - step : step;
+    LevelArgs a{};
+    level_dims(p, k, a);
+    // the four subband planes of this level inside the Mallat-packed buffer
+    const void* coef = inverse ? src : dst;
+    const size_t cp = inverse ? src_pitch : dst_pitch;
+    const char* cb = static_cast<const char*>(coef);
+    const void* band[4];
+    long long bpitch[4];
+    band[1] = cb + a.cw * es;
+    band[2] = cb + a.ch * cp;
+    band[3] = cb + a.ch * cp + a.cw * es;
+    for (int i = 1; i < 4; ++i) bpitch[i] = (long long)(cp / es);
+    // LL of this level: the next level's input (scratch) or, at the last
+    // level, the top-left quadrant of the coefficient buffer
+    if (k == Lv - 1) {
+      band[0] = coef;
+      bpitch[0] = (long long)(cp / es);
+    } else {
+      band[0] = p->scratch[k & 1];
+      bpitch[0] = (long long)(p->scratch_pitch / es);
+    }
+    // the level's sample plane: image (level 0) or scratch
+    const void* samples;
+    long long spitch;
+    if (k == 0) {
+      samples = inverse ? dst : src;
+      spitch = (long long)((inverse ? dst_pitch : src_pitch) / es);
+    } else {
+      samples = p->scratch[(k - 1) & 1];
+      spitch = (long long)(p->scratch_pitch / es);
+    }
+    const Coefs cf = make_coefs(L, p->norm, a.W, a.H, PASS_FUSED, inverse);
+    ConvTaps ct;
+    std::memset(&ct, 0, sizeof ct);
+    if (scheme == DWT_CONVOLUTION && !conv_taps(L, p->norm, a.W, a.H, inverse, &ct))
+      return DWT_EUNSUPPORTED;
+    dwt_status st;
+    if (scheme != DWT_ROWCOL) {
+      LaunchKey key{p->wavelet, p->dtype, scheme, PASS_FUSED, inverse ? 1 : 0};
+      if (!inverse) {
+        a.src[0] = samples;
+        a.src_pitch[0] = spitch;
+        for (int i = 0; i < 4; ++i) {
+          a.dst[i] = const_cast<void*>(band[i]);
+          a.dst_pitch[i] = bpitch[i];
+        }
+      } else {
+        for (int i = 0; i < 4; ++i) {
+          a.src[i] = band[i];
+          a.src_pitch[i] = bpitch[i];
+        }
+        a.dst[0] = const_cast<void*>(samples);
+        a.dst_pitch[0] = spitch;
+      }
+      std::snprintf(slot, sizeof slot, "%s/L%d", inverse ? "inv" : "fwd", k);
+      st = launch(p, key, a, cf, ct, s, slot);
+    } else {
+      // row-column: vertical pass and horizontal pass through p->tmp
+      const long long tp = (long long)(p->tmp_pitch / es);
+      LevelArgs v = a, hz = a;
+      const Coefs cv = make_coefs(L, p->norm, a.W, a.H, PASS_VERT, inverse);
+      const Coefs chz = make_coefs(L, p->norm, a.W, a.H, PASS_HORZ, inverse);
+      LaunchKey kv{p->wavelet, p->dtype, DWT_ROWCOL, PASS_VERT, inverse ? 1 : 0};
+      LaunchKey kh{p->wavelet, p->dtype, DWT_ROWCOL, PASS_HORZ, inverse ? 1 : 0};
+      if (!inverse) {
+        v.src[0] = samples;
+        v.src_pitch[0] = spitch;
+        v.dst[0] = p->tmp;
+        v.dst_pitch[0] = tp;
+        hz.src[0] = p->tmp;
+        hz.src_pitch[0] = tp;
+        for (int i = 0; i < 4; ++i) {
+          hz.dst[i] = const_cast<void*>(band[i]);
+          hz.dst_pitch[i] = bpitch[i];
+        }
+        std::snprintf(slot, sizeof slot, "fwd-v/L%d", k);
+        st = launch(p, kv, v, cv, ct, s, slot);
+        if (st != DWT_OK) return st;
+        std::snprintf(slot, sizeof slot, "fwd-h/L%d", k);
+        st = launch(p, kh, hz, chz, ct, s, slot);
+      } else {
+        for (int i = 0; i < 4; ++i) {
+          hz.src[i] = band[i];
+          hz.src_pitch[i] = bpitch[i];
+        }
+        hz.dst[0] = p->tmp;
+        hz.dst_pitch[0] = tp;
+        v.src[0] = p->tmp;
+        v.src_pitch[0] = tp;
+        v.dst[0] = const_cast<void*>(samples);
+        v.dst_pitch[0] = spitch;
+        std::snprintf(slot, sizeof slot, "inv-h/L%d", k);
+        st = launch(p, kh, hz, chz, ct, s, slot);
+        if (st != DWT_OK) return st;
+        std::snprintf(slot, sizeof slot, "inv-v/L%d", k);
+        st = launch(p, kv, v, cv, ct, s, slot);
+      }
+    }
+    if (st != DWT_OK) return st;
+  }
+  return DWT_OK;
+}
+
+struct DeviceGuard {
+  int prev = -1;
+  bool ok = false;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) == cudaSuccess) ok = prev == dev || cudaSetDevice(dev) == cudaSuccess;
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+const char* dwt_version(void) { return "0.1.0"; }
+
+const char* dwt_status_string(dwt_status s) {
+  switch (s) {
+    case DWT_OK: return "ok";
+    case DWT_EINVAL: return "invalid argument";
+    case DWT_ENOMEM: return "out of memory";
+    case DWT_EUNSUPPORTED: return "unsupported combination";
+    case DWT_ECUDA: return "CUDA error";
+    case DWT_ETIMEOUT: return "device-side wait timed out";
+    case DWT_EBUSY: return "resource busy";
+  }
+  return "unknown status";
+}
+
+dwt_status dwt_plan_create(int w, int h, dwt_wavelet wavelet, int levels, dwt_dtype dtype,
+                           dwt_plan* out) {
+  if (!out) return DWT_EINVAL;
+  *out = nullptr;
+  if (w < 1 || h < 1 || levels < 0) return DWT_EINVAL;
+  if ((int)wavelet < 0 || (int)wavelet > 2 || (int)dtype < 0 || (int)dtype > 2) return DWT_EINVAL;
+  int maxl = 0;
+  for (int a = w, b = h; a > 1 || b > 1; a = (a + 1) / 2, b = (b + 1) / 2) ++maxl;
+  if (levels > maxl) return DWT_EINVAL;
+  if (dtype == DWT_I32 && wavelet != DWT_CDF53) return DWT_EUNSUPPORTED;
+  if (wavelet == DWT_DD137) return DWT_EUNSUPPORTED;
+  dwt_plan_s* p = new (std::nothrow) dwt_plan_s();
+  if (!p) return DWT_ENOMEM;
+  p->w = w;
+  p->h = h;
+  p->levels = levels;
+  p->wavelet = wavelet;
+  p->dtype = dtype;
+  p->es = elem_size(dtype);
+  if (cudaGetDevice(&p->device) != cudaSuccess) {
+    delete p;
+    return DWT_ECUDA;
+  }
+  p->W.resize(levels + 2);
+  p->H.resize(levels + 2);
+  p->W[0] = w;
+  p->H[0] = h;
+  for (int k = 1; k <= levels + 1; ++k) {
+    p->W[k] = (p->W[k - 1] + 1) / 2;
+    p->H[k] = (p->H[k - 1] + 1) / 2;
+  }
+  cudaError_t e = cudaMalloc(&p->d_status, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(p->d_status, 0, sizeof(int));
+  if (e == cudaSuccess && levels >= 2) {
+    p->scratch_pitch = round_up((size_t)p->W[1] * p->es, 128);
+    e = cudaMalloc(&p->scratch[0], p->scratch_pitch * p->H[1]);
+    if (e == cudaSuccess) e = cudaMalloc(&p->scratch[1], p->scratch_pitch * p->H[2]);
+  }
+  if (e != cudaSuccess) {
+    dwt_plan_destroy(p);
+    return from_cuda(e);
+  }
+  *out = p;
+  return DWT_OK;
+}
+
+dwt_status dwt_plan_set_scheme(dwt_plan p, dwt_scheme scheme) {
+  if (!p) return DWT_EINVAL;
+  if ((int)scheme < 0 || (int)scheme >= NUM_SCHEMES) return DWT_EINVAL;
+  if (scheme != DWT_AUTO && !scheme_supported(p->wavelet, p->dtype, scheme)) return DWT_EUNSUPPORTED;
+  std::lock_guard<std::mutex> lk(p->mu);
+  p->scheme = scheme;
+  if (scheme == DWT_ROWCOL && p->levels > 0) {
+    DeviceGuard g(p->device);
+    return ensure_tmp(p);
+  }
+  return DWT_OK;
+}
+
+dwt_status dwt_plan_get_scheme(dwt_plan p, dwt_scheme* scheme) {
+  if (!p || !scheme) return DWT_EINVAL;
+  std::lock_guard<std::mutex> lk(p->mu);
+  *scheme = (dwt_scheme)resolve_scheme(p);
+  return DWT_OK;
+}
+
+dwt_status dwt_plan_set_normalization(dwt_plan p, dwt_norm norm) {
+  if (!p || ((int)norm != DWT_NORM_JPEG2000 && (int)norm != DWT_NORM_ZETA)) return DWT_EINVAL;
+  if (p->dtype == DWT_I32 && norm != DWT_NORM_JPEG2000) return DWT_EUNSUPPORTED;
+  std::lock_guard<std::mutex> lk(p->mu);
+  p->norm = norm;
+  return DWT_OK;
+}
+
+dwt_status dwt2_forward(dwt_plan p, const void* d_in, size_t in_pitch, void* d_out, size_t out_pitch,
+                        dwt_stream stream) {
+  if (!p) return DWT_EINVAL;
+  std::lock_guard<std::mutex> lk(p->mu);
+  return run(p, false, d_in, in_pitch, d_out, out_pitch, reinterpret_cast<cudaStream_t>(stream));
+}
+
+dwt_status dwt2_inverse(dwt_plan p, const void* d_coef, size_t coef_pitch, void* d_out,
+                        size_t out_pitch, dwt_stream stream) {
+  if (!p) return DWT_EINVAL;
+  std::lock_guard<std::mutex> lk(p->mu);
+  return run(p, true, d_coef, coef_pitch, d_out, out_pitch, reinterpret_cast<cudaStream_t>(stream));
+}
+
+static dwt_status host_call(dwt_plan p, bool inverse, const void* h_in, size_t in_pitch, void* h_out,
+                            size_t out_pitch, dwt_stream stream) {
+  if (!p || !h_in || !h_out) return DWT_EINVAL;
+  std::lock_guard<std::mutex> lk(p->mu);
+  const size_t row = (size_t)p->w * p->es;
+  if (in_pitch < row || out_pitch < row) return DWT_EINVAL;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (!p->stage_in) {
+    p->stage_pitch = round_up(row, 128);
+    cudaError_t e = cudaMalloc(&p->stage_in, p->stage_pitch * p->h);
+    if (e == cudaSuccess) e = cudaMalloc(&p->stage_out, p->stage_pitch * p->h);
+    if (e != cudaSuccess) return from_cuda(e);
+  }
+  cudaError_t e = cudaMemcpy2DAsync(p->stage_in, p->stage_pitch, h_in, in_pitch, row, p->h,
+                                    cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return from_cuda(e);
+  dwt_status st = run(p, inverse, p->stage_in, p->stage_pitch, p->stage_out, p->stage_pitch, s);
+  if (st != DWT_OK) return st;
+  return from_cuda(cudaMemcpy2DAsync(h_out, out_pitch, p->stage_out, p->stage_pitch, row, p->h,
+                                     cudaMemcpyDeviceToHost, s));
+}
+
+dwt_status dwt2_forward_host(dwt_plan p, const void* h_in, size_t in_pitch, void* h_out,
+                             size_t out_pitch, dwt_stream stream) {
+  return host_call(p, false, h_in, in_pitch, h_out, out_pitch, stream);
+}
+
+dwt_status dwt2_inverse_host(dwt_plan p, const void* h_coef, size_t coef_pitch, void* h_out,
+                             size_t out_pitch, dwt_stream stream) {
+  return host_call(p, true, h_coef, coef_pitch, h_out, out_pitch, stream);
+}
+
+dwt_status dwt_batch_submit(const dwt_request* reqs, int n, dwt_stream stream, int* d_status) {
+  if (n < 0 || (n > 0 && !reqs)) return DWT_EINVAL;
+  for (int i = 0; i < n; ++i) {
+    if (!reqs[i].plan) return DWT_EINVAL;
+    for (int j = 0; j < i; ++j)
+      if (reqs[j].plan == reqs[i].plan) return DWT_EBUSY;
+  }
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  for (int i = 0; i < n; ++i) {
+    dwt_plan p = reqs[i].plan;
+    std::lock_guard<std::mutex> lk(p->mu);
+    dwt_status st = run(p, reqs[i].inverse != 0, reqs[i].in, reqs[i].in_pitch, reqs[i].out,
+                        reqs[i].out_pitch, s);
+    if (st != DWT_OK) return st;
+  }
+  if (d_status && n > 0) return from_cuda(cudaMemsetAsync(d_status, 0, sizeof(int) * n, s));
+  return DWT_OK;
+}
+
+dwt_status dwt_plan_device_status(dwt_plan p) {
+  if (!p) return DWT_EINVAL;
+  std::lock_guard<std::mutex> lk(p->mu);
+  int v = 0;
+  cudaError_t e = cudaStreamSynchronize(p->last_stream);
+  if (e == cudaSuccess) e = cudaMemcpy(&v, p->d_status, sizeof v, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && v) e = cudaMemset(p->d_status, 0, sizeof(int));
+  if (e != cudaSuccess) return from_cuda(e);
+  return v ? DWT_ETIMEOUT : DWT_OK;
+}
+
+dwt_status dwt_plan_set_profiling(dwt_plan p, int enable) {
+  if (!p) return DWT_EINVAL;
+  std::lock_guard<std::mutex> lk(p->mu);
+  p->profiling = enable != 0;
+  return DWT_OK;
+}
+
+dwt_status dwt_plan_read_profile(dwt_plan p, dwt_kernel_stat* stats, int capacity, int* count) {
+  if (!p || (capacity > 0 && !stats)) return DWT_EINVAL;
+  std::lock_guard<std::mutex> lk(p->mu);
+  for (const ProfRec& r : p->pending) {
+    float ms = 0.f;
+    if (cudaEventSynchronize(r.b) == cudaSuccess && cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+      p->slots[r.slot].launches += 1;
+      p->slots[r.slot].ms += ms;
+      p->slots[r.slot].bytes += r.bytes;
+    }
+    p->pool.push_back(r.a);
+    p->pool.push_back(r.b);
+  }
+  p->pending.clear();
+  const int n = (int)p->slots.size();
+  for (int i = 0; i < n && i < capacity; ++i) {
+    std::memset(&stats[i], 0, sizeof stats[i]);
+    std::snprintf(stats[i].name, sizeof stats[i].name, "%s", p->slots[i].name.c_str());
+    stats[i].launches = p->slots[i].launches;
+    stats[i].total_ms = p->slots[i].ms;
+    stats[i].algorithmic_bytes = p->slots[i].bytes;
+  }
+  if (count) *count = n;
+  p->slots.clear();
+  return DWT_OK;
+}
+
+dwt_status dwt_plan_autotune(dwt_plan p, dwt_stream stream) {
+  if (!p) return DWT_EINVAL;
+  std::lock_guard<std::mutex> lk(p->mu);
+  if (p->levels == 0) return DWT_OK;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const size_t pitch = round_up((size_t)p->w * p->es, 128);
+  void *in = nullptr, *out = nullptr;
+  cudaError_t e = cudaMalloc(&in, pitch * p->h);
+  if (e == cudaSuccess) e = cudaMalloc(&out, pitch * p->h);
+  if (e == cudaSuccess) e = cudaMemsetAsync(in, 0x3c, pitch * p->h, s);
+  cudaEvent_t a = nullptr, b = nullptr;
+  if (e == cudaSuccess) e = cudaEventCreate(&a);
+  if (e == cudaSuccess) e = cudaEventCreate(&b);
+  int best = -1;
+  float best_ms = 0.f;
+  const int saved = p->scheme;
+  const bool saved_prof = p->profiling;
+  p->profiling = false;
+  for (int sc = DWT_ROWCOL; e == cudaSuccess && sc < NUM_SCHEMES; ++sc) {
+    if (!scheme_supported(p->wavelet, p->dtype, sc)) continue;
+    p->scheme = sc;
+    if (sc == DWT_ROWCOL && ensure_tmp(p) != DWT_OK) continue;
+    float t = 1e30f;
+    bool ok = true;
+    for (int rep = 0; rep < 5 && ok; ++rep) {
+      cudaEventRecord(a, s);
+      ok = run(p, false, in, pitch, out, pitch, s) == DWT_OK;
+      cudaEventRecord(b, s);
+      if (ok && cudaEventSynchronize(b) == cudaSuccess) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, a, b);
+        if (rep >= 2) t = std::min(t, ms);
+      }
+    }
+    if (ok && (best < 0 || t < best_ms)) {
+      best = sc;
+      best_ms = t;
+    }
+  }
+  p->scheme = saved;
+  p->profiling = saved_prof;
+  if (a) cudaEventDestroy(a);
+  if (b) cudaEventDestroy(b);
+  cudaFree(in);
+  cudaFree(out);
+  if (e != cudaSuccess) return from_cuda(e);
+  if (best < 0) return DWT_EUNSUPPORTED;
+  p->auto_scheme = best;
+  cache_store(cache_key(p), best);
+  return DWT_OK;
+}
+
+dwt_status dwt_plan_destroy(dwt_plan p) {
+  if (!p) return DWT_EINVAL;
+  {
+    DeviceGuard g(p->device);
+    if (p->last_stream || !p->pending.empty()) cudaDeviceSynchronize();
+    for (void* q : {p->scratch[0], p->scratch[1], p->tmp, p->stage_in, p->stage_out,
+                    static_cast<void*>(p->d_status)})
+      if (q) cudaFree(q);
+    for (const ProfRec& r : p->pending) {
+      cudaEventDestroy(r.a);
+      cudaEventDestroy(r.b);
+    }
+    for (cudaEvent_t ev : p->pool) cudaEventDestroy(ev);
+  }
+  delete p;
+  return DWT_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,116 @@
+// Internal interface between the host API (dwt_api.cpp) and the kernel
+// translation units.  Not part of the public ABI.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace dwt {
+
+// Storage types (match dwt_dtype).
+enum DType : int { F32 = 0, F16S = 1, I32 = 2 };
+// Wavelets (match dwt_wavelet).
+enum Wavelet : int { W53 = 0, W97 = 1, WDD = 2 };
+// Schemes (match dwt_scheme).
+enum Scheme : int {
+  AUTO = 0, ROWCOL, SWELDENS, IWAHASHI, IWAHASHI_S, EXPLOSIVE, EXPLOSIVE_S,
+  MONOLITHIC, MONOLITHIC_S, POLYPHASE, POLYPHASE_S, CONVOLUTION, NUM_SCHEMES
+};
+
+// What a launch reads and writes.
+//  SAMPLES:  one interleaved sample plane (image, or a row-column intermediate)
+//  SUBBANDS: four planes LL, HL, LH, HH (Mallat quadrants / scratch LL)
+enum Layout : int { SAMPLES = 0, SUBBANDS = 1 };
+
+// Pass kinds of a launch.
+enum Pass : int {
+  PASS_FUSED = 0,   // one launch per level: the whole 2-D scheme
+  PASS_VERT = 1,    // row-column baseline: vertical 1-D transform
+  PASS_HORZ = 2     // row-column baseline: horizontal 1-D transform
+};
+
+constexpr int kWarpsPerCta = 4;  // independent warps (one strip each) per CTA
+constexpr int kChunkRows = 4;    // quad rows per pipeline stage
+constexpr int kMaxStages = 4;    // ring depth per warp
+
+// Lifting coefficients per predict/update pair and axis.  A coefficient of
+// an axis whose length is 1 is zero, which makes that axis' lifting the
+// identity (a length-1 line is left untouched).
+struct Coefs {
+  float ph1[2], ph3[2], uh1[2], uh3[2];  // horizontal: taps at distance 1 and 3 (samples)
+  float pv1[2], pv3[2], uv1[2], uv3[2];  // vertical
+  float scale[4];                        // LL, HL, LH, HH (forward); reciprocals for the inverse
+  int v_on, h_on;                        // integer path: axis has length > 1
+};
+
+// 2-D taps of the Convolution scheme, indexed
+// [out row type][out col type][in row type][in col type][dy + 2][dx + 2].
+// Forward: out types are (L, H) bands, in types (even, odd) polyphase
+// components; inverse: the other way round.  Scaling is folded in.
+struct ConvTaps {
+  float t[2][2][2][2][5][5];
+};
+
+// Geometry and buffers of one launch (one level, one pass).
+struct LevelArgs {
+  // Dimensions of the level's sample plane (forward input / inverse output).
+  int W, H;
+  int cw, ch;  // ceil(W/2), ceil(H/2): quads / LL size
+  int fw, fh;  // floor(W/2), floor(H/2)
+  // Strips: column strip cs covers useful quads [cs*UQ, cs*UQ+UQ); row
+  // strip rs covers quad rows [rs*T, rs*T+T).
+  int ncs, nrs, T;
+  int nstages;  // ring depth used (<= kMaxStages)
+  // Sources and destinations (element pitches).
+  const void* src[4];
+  long long src_pitch[4];
+  void* dst[4];
+  long long dst_pitch[4];
+  int src_tma;   // 1: tensor maps are valid for every source plane
+  int* status;   // device error word (bit 0: a bounded wait ran out)
+};
+
+struct TmaMaps {
+  CUtensorMap m[4];
+};
+
+// Properties a host needs to lay out a launch: horizontal halo quads per
+// side (HQ), useful quads per warp (UQ), dynamic shared memory per CTA, and
+// the loader/storer layouts.
+struct KernelInfo {
+  int hq;
+  int uq;
+  int up, down;  // vertical halo (quad rows) above / below
+  Layout load, store;
+  int box_w, box_h;  // TMA box of one source plane (elements x rows)
+  size_t smem_bytes;
+  const void* fn;  // kernel entry (for occupancy queries)
+  bool supported;
+};
+
+struct LaunchKey {
+  int wavelet, dtype, scheme, pass, inverse;
+};
+
+struct LaunchCall {
+  const LevelArgs* a;
+  const TmaMaps* maps;
+  const Coefs* cf;
+  const ConvTaps* ct;
+  cudaStream_t stream;
+};
+
+// Returns true when the group handles `k`; then fills *info and/or launches.
+using GroupFn = bool (*)(const LaunchKey& k, int nstages, KernelInfo* info, const LaunchCall* call,
+                         cudaError_t* err);
+
+bool group_sweldens(const LaunchKey&, int, KernelInfo*, const LaunchCall*, cudaError_t*);
+bool group_iwahashi(const LaunchKey&, int, KernelInfo*, const LaunchCall*, cudaError_t*);
+bool group_explosive(const LaunchKey&, int, KernelInfo*, const LaunchCall*, cudaError_t*);
+bool group_monolithic(const LaunchKey&, int, KernelInfo*, const LaunchCall*, cudaError_t*);
+bool group_polyphase(const LaunchKey&, int, KernelInfo*, const LaunchCall*, cudaError_t*);
+bool group_convolution(const LaunchKey&, int, KernelInfo*, const LaunchCall*, cudaError_t*);
+bool group_rowcol(const LaunchKey&, int, KernelInfo*, const LaunchCall*, cudaError_t*);
+
+}  // namespace dwt

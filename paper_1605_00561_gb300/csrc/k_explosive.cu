@@ -1,0 +1,14 @@
+// Kernels of the EXPLOSIVE and EXPLOSIVE_S scheme(s): forward and inverse, CDF 5/3 and 9/7,
+// float32 and float16-storage.
+#include "dispatch.cuh"
+
+namespace dwt {
+
+bool group_explosive(const LaunchKey& k, int ns, KernelInfo* info, const LaunchCall* call,
+                   cudaError_t* err) {
+  if (dev::fused_float<EXPLOSIVE>(k, ns, info, call, err)) return true;
+  if (dev::fused_float<EXPLOSIVE_S>(k, ns, info, call, err)) return true;
+  return false;
+}
+
+}  // namespace dwt

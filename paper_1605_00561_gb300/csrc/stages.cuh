@@ -1,0 +1,360 @@
+// Lifting steps of the paper as compile-time stencil stages.
+//
+// A quadruple (n, m) holds the samples of rows 2n..2n+1 and columns
+// 2m..2m+1: LL (even, even), HL (even, odd), LH (odd, even), HH (odd, odd)
+// (Sec. 2.3).  A lane of a warp holds two horizontally adjacent
+// quadruples ("a" = 2l, "b" = 2l+1 relative to the warp's first quad), so a
+// horizontal neighbour at distance <= 2 is either in the lane or one shuffle
+// away.  Vertical neighbours come from the stage's window of rows.
+//
+// A linear stage is one step matrix of the paper: every target subband
+// receives sum(sign * (vertical op (x) horizontal op) applied to a source
+// subband), all sources read from the pre-step state (the matrices act on
+// the whole vector at once, Sec. 2.4).  The 1-D operators are the predict P
+// and update U of Sec. 2.2 / Sec. 5, their scalar split P = P0 + P1,
+// U = U0 + U1 (Sec. 4), V = PU + 1 (Sec. 2.3) and the identity.  With P
+// placed after L (JPEG 2000 origin) the predict reads quads at offsets
+// {0, +1} and the update reads {-1, 0}.
+#pragma once
+
+#include <type_traits>
+
+#include "dwt_internal.h"
+
+namespace dwt {
+namespace dev {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+template <int B, int E, class F>
+__device__ __forceinline__ void static_for(F&& f) {
+  if constexpr (B <= E) {
+    f(std::integral_constant<int, B>{});
+    static_for<B + 1, E>(f);
+  }
+}
+
+__host__ __device__ constexpr int cmax(int a, int b) { return a > b ? a : b; }
+__host__ __device__ constexpr int cmin(int a, int b) { return a < b ? a : b; }
+template <class... A>
+__host__ __device__ constexpr int vmax(int a, A... b) {
+  int r = a;
+  ((r = b > r ? b : r), ...);
+  return r;
+}
+template <class... A>
+__host__ __device__ constexpr int vmin(int a, A... b) {
+  int r = a;
+  ((r = b < r ? b : r), ...);
+  return r;
+}
+
+enum Sub : int { LL = 0, HL = 1, LH = 2, HH = 3 };
+
+template <typename V>
+struct Row {
+  V s[4][2];
+};
+
+// The value of the quad at position P, where 0 and 1 are this lane's quads
+// a and b, -2/-1 the previous lane's and 2/3 the next lane's.
+template <int P, typename V>
+__device__ __forceinline__ V hpos(const V (&x)[2]) {
+  static_assert(P >= -2 && P <= 3, "horizontal reach beyond the neighbouring lane");
+  if constexpr (P == 0) return x[0];
+  else if constexpr (P == 1) return x[1];
+  else if constexpr (P == -1) return __shfl_up_sync(kFull, x[1], 1);
+  else if constexpr (P == -2) return __shfl_up_sync(kFull, x[0], 1);
+  else if constexpr (P == 2) return __shfl_down_sync(kFull, x[0], 1);
+  else return __shfl_down_sync(kFull, x[1], 1);
+}
+
+// ---------------------------------------------------------------------------
+// 1-D operators
+// ---------------------------------------------------------------------------
+enum Op : int { OP_I, OP_P, OP_U, OP_P0, OP_P1, OP_U0, OP_U1, OP_V, OP_V1 };
+
+// Degree-1 lifting (CDF 5/3 and 9/7): P = p(1 + z), U = u(1 + z^-1) in the
+// quad-offset convention above.  Degree 3 (DD 13/7): P has taps p1 at 0, +1
+// and p3 at -1, +2; U has u1 at -1, 0 and u3 at -2, +1.
+template <int DEG, int OP>
+struct OpShape {
+  static constexpr int lo = (OP == OP_I || OP == OP_P0 || OP == OP_U0 || OP == OP_V1) ? 0
+                            : (OP == OP_P)  ? (DEG == 1 ? 0 : -1)
+                            : (OP == OP_P1) ? (DEG == 1 ? 1 : -1)
+                            : (OP == OP_U)  ? (DEG == 1 ? -1 : -2)
+                            : (OP == OP_U1) ? (DEG == 1 ? -1 : -2)
+                                            : -1;  // OP_V (degree 1)
+  static constexpr int hi = (OP == OP_I || OP == OP_P0 || OP == OP_U0 || OP == OP_V1) ? 0
+                            : (OP == OP_P)  ? (DEG == 1 ? 1 : 2)
+                            : (OP == OP_P1) ? (DEG == 1 ? 1 : 2)
+                            : (OP == OP_U)  ? (DEG == 1 ? 0 : 1)
+                            : (OP == OP_U1) ? (DEG == 1 ? -1 : 1)
+                                            : 1;
+  // The split operators P1, U1 of degree 3 have a zero tap at offset 0.
+  __host__ __device__ static constexpr bool has(int off) {
+    return !((OP == OP_P1 || OP == OP_U1) && DEG == 3 && off == 0);
+  }
+};
+
+// Coefficient of operator OP (pair K, axis: 0 vertical, 1 horizontal) at
+// quad offset OFF.
+template <int DEG, int OP, int K, int AXIS, int OFF>
+__device__ __forceinline__ float op_tap(const Coefs& c) {
+  const float p1 = AXIS ? c.ph1[K] : c.pv1[K];
+  const float u1 = AXIS ? c.uh1[K] : c.uv1[K];
+  if constexpr (OP == OP_I) {
+    return 1.0f;
+  } else if constexpr (OP == OP_P || OP == OP_P1) {
+    if constexpr (DEG == 1) return p1;
+    else return (OFF == 0 || OFF == 1) ? p1 : (AXIS ? c.ph3[K] : c.pv3[K]);
+  } else if constexpr (OP == OP_P0) {
+    return p1;
+  } else if constexpr (OP == OP_U || OP == OP_U1) {
+    if constexpr (DEG == 1) return u1;
+    else return (OFF == -1 || OFF == 0) ? u1 : (AXIS ? c.uh3[K] : c.uv3[K]);
+  } else if constexpr (OP == OP_U0) {
+    return u1;
+  } else if constexpr (OP == OP_V) {  // V = PU + 1: pu z^-1 + (1 + 2pu) + pu z
+    static_assert(DEG == 1, "V of degree 3 reaches beyond one lane");
+    return OFF == 0 ? 1.0f + 2.0f * p1 * u1 : p1 * u1;
+  } else {  // OP_V1 = P1 U1 + 1 = 1 + pu (degree 1)
+    static_assert(DEG == 1, "V1 of degree 3 reaches beyond one lane");
+    return 1.0f + p1 * u1;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Linear stages (one step matrix)
+// ---------------------------------------------------------------------------
+template <int TGT, int SRC, int VOP, int HOP, int SGN = 1>
+struct Term {
+  static constexpr int tgt = TGT, src = SRC, vop = VOP, hop = HOP, sgn = SGN;
+};
+
+template <int DEG, int K, bool REPLACE, class... Ts>
+struct Lin {
+  static constexpr int UP = -vmin(0, OpShape<DEG, Ts::vop>::lo...);
+  static constexpr int DOWN = vmax(0, OpShape<DEG, Ts::vop>::hi...);
+  static constexpr int LEFT = -vmin(0, OpShape<DEG, Ts::hop>::lo...);
+  static constexpr int RIGHT = vmax(0, OpShape<DEG, Ts::hop>::hi...);
+  static constexpr unsigned TARGETS = (0u | ... | (1u << Ts::tgt));
+
+  template <class T>
+  __device__ __forceinline__ static void term(const Row<float>* w, Row<float>& o, const Coefs& c) {
+    using VS = OpShape<DEG, T::vop>;
+    using HS = OpShape<DEG, T::hop>;
+    static_for<VS::lo, VS::hi>([&](auto dy) {
+      constexpr int DY = decltype(dy)::value;
+      if constexpr (VS::has(DY)) {
+        const float(&x)[2] = w[UP + DY].s[T::src];
+        static_for<HS::lo, HS::hi>([&](auto dx) {
+          constexpr int DX = decltype(dx)::value;
+          if constexpr (HS::has(DX)) {
+            const float cf = (T::sgn > 0 ? 1.0f : -1.0f) * op_tap<DEG, T::vop, K, 0, DY>(c) *
+                             op_tap<DEG, T::hop, K, 1, DX>(c);
+            o.s[T::tgt][0] = fmaf(cf, hpos<0 + DX>(x), o.s[T::tgt][0]);
+            o.s[T::tgt][1] = fmaf(cf, hpos<1 + DX>(x), o.s[T::tgt][1]);
+          }
+        });
+      }
+    });
+  }
+
+  __device__ __forceinline__ static void eval(const Row<float>* w, Row<float>& o, const Coefs& c,
+                                              const ConvTaps&) {
+    o = w[UP];
+    if constexpr (REPLACE) {
+#pragma unroll
+      for (int s = 0; s < 4; ++s)
+        if (TARGETS & (1u << s)) o.s[s][0] = o.s[s][1] = 0.0f;
+    }
+    (term<Ts>(w, o, c), ...);
+  }
+};
+
+// Scaling step (Sec. 2.2, the diagonal matrix of M): per-subband factors.
+struct Scale {
+  static constexpr int UP = 0, DOWN = 0, LEFT = 0, RIGHT = 0;
+  __device__ __forceinline__ static void eval(const Row<float>* w, Row<float>& o, const Coefs& c,
+                                              const ConvTaps&) {
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+      o.s[s][0] = w[0].s[s][0] * c.scale[s];
+      o.s[s][1] = w[0].s[s][1] * c.scale[s];
+    }
+  }
+};
+
+// ---------------------------------------------------------------------------
+// Convolution scheme (Sec. 2.3): each output polyphase component is a 2-D
+// FIR of the four input components; the taps (scaling folded in) are the
+// products of the 1-D polyphase entries of the whole factorisation, indexed
+// [out row][out col][in row][in col][dy][dx].
+// ---------------------------------------------------------------------------
+template <int WL, bool INV>
+struct ConvShape {
+  // [out][in] ranges of the 1-D polyphase entries (quad offsets).
+  __host__ __device__ static constexpr int lo(int o, int i) {
+    return WL == W53 ? (!INV ? (o == 0 ? -1 : 0) : (i == 0 ? 0 : -1))
+                     : (!INV ? (o == 0 ? -2 : -1) : (i == 0 ? -1 : -2));
+  }
+  __host__ __device__ static constexpr int hi(int o, int i) {
+    return WL == W53 ? (!INV ? (o == 0 ? (i == 0 ? 1 : 0) : (i == 0 ? 1 : 0))
+                             : (o == 0 ? 0 : (i == 0 ? 1 : 1)))
+                     : (!INV ? (o == 0 ? (i == 0 ? 2 : 1) : (i == 0 ? 2 : 1))
+                             : (o == 0 ? 1 : 2));
+  }
+};
+
+template <int WL, bool INV>
+struct Conv {
+  using S = ConvShape<WL, INV>;
+  static constexpr int UP = -cmin(cmin(S::lo(0, 0), S::lo(0, 1)), cmin(S::lo(1, 0), S::lo(1, 1)));
+  static constexpr int DOWN = cmax(cmax(S::hi(0, 0), S::hi(0, 1)), cmax(S::hi(1, 0), S::hi(1, 1)));
+  static constexpr int LEFT = UP, RIGHT = DOWN;
+
+  __device__ __forceinline__ static void eval(const Row<float>* w, Row<float>& o, const Coefs&,
+                                              const ConvTaps& t) {
+    static_for<0, 3>([&](auto so_sx) {
+      constexpr int SO = decltype(so_sx)::value >> 1, SX = decltype(so_sx)::value & 1;
+      float acc0 = 0.0f, acc1 = 0.0f;
+      static_for<0, 3>([&](auto ti_tx) {
+        constexpr int TI = decltype(ti_tx)::value >> 1, TX = decltype(ti_tx)::value & 1;
+        static_for<S::lo(SO, TI), S::hi(SO, TI)>([&](auto dy) {
+          constexpr int DY = decltype(dy)::value;
+          const float(&x)[2] = w[UP + DY].s[2 * TI + TX];
+          static_for<S::lo(SX, TX), S::hi(SX, TX)>([&](auto dx) {
+            constexpr int DX = decltype(dx)::value;
+            const float cf = t.t[SO][SX][TI][TX][DY + 2][DX + 2];
+            acc0 = fmaf(cf, hpos<0 + DX>(x), acc0);
+            acc1 = fmaf(cf, hpos<1 + DX>(x), acc1);
+          });
+        });
+      });
+      o.s[2 * SO + SX][0] = acc0;
+      o.s[2 * SO + SX][1] = acc1;
+    });
+  }
+};
+
+// ---------------------------------------------------------------------------
+// Reversible integer 5/3, JPEG 2000 floor rounding, separable order:
+// vertical predict, vertical update, horizontal predict, horizontal update.
+// ---------------------------------------------------------------------------
+template <int KIND, bool INV>
+struct Int53 {
+  // KIND 0: vertical predict (reads rows n, n+1), 1: vertical update
+  // (rows n-1, n), 2: horizontal predict (quads m, m+1), 3: horizontal update.
+  static constexpr int UP = KIND == 1 ? 1 : 0;
+  static constexpr int DOWN = KIND == 0 ? 1 : 0;
+  static constexpr int LEFT = KIND == 3 ? 1 : 0;
+  static constexpr int RIGHT = KIND == 2 ? 1 : 0;
+
+  __device__ __forceinline__ static void eval(const Row<int>* w, Row<int>& o, const Coefs& c,
+                                              const ConvTaps&) {
+    o = w[UP];
+    const int sg = INV ? -1 : 1;
+    if constexpr (KIND == 0) {  // odd rows -= floor((even above + even below) / 2)
+      if (c.v_on) {
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+          o.s[LH][j] -= sg * ((w[0].s[LL][j] + w[1].s[LL][j]) >> 1);
+          o.s[HH][j] -= sg * ((w[0].s[HL][j] + w[1].s[HL][j]) >> 1);
+        }
+      }
+    } else if constexpr (KIND == 1) {  // even rows += floor((odd above + odd below + 2) / 4)
+      if (c.v_on) {
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+          o.s[LL][j] += sg * ((w[0].s[LH][j] + w[1].s[LH][j] + 2) >> 2);
+          o.s[HL][j] += sg * ((w[0].s[HH][j] + w[1].s[HH][j] + 2) >> 2);
+        }
+      }
+    } else if constexpr (KIND == 2) {
+      if (c.h_on) {
+        const int* ll = w[0].s[LL];
+        const int* lh = w[0].s[LH];
+        const int llr = hpos<2>(w[0].s[LL]), lhr = hpos<2>(w[0].s[LH]);
+        o.s[HL][0] -= sg * ((ll[0] + ll[1]) >> 1);
+        o.s[HL][1] -= sg * ((ll[1] + llr) >> 1);
+        o.s[HH][0] -= sg * ((lh[0] + lh[1]) >> 1);
+        o.s[HH][1] -= sg * ((lh[1] + lhr) >> 1);
+      }
+    } else {
+      if (c.h_on) {
+        const int* hl = w[0].s[HL];
+        const int* hh = w[0].s[HH];
+        const int hll = hpos<-1>(w[0].s[HL]), hhl = hpos<-1>(w[0].s[HH]);
+        o.s[LL][0] += sg * ((hll + hl[0] + 2) >> 2);
+        o.s[LL][1] += sg * ((hl[0] + hl[1] + 2) >> 2);
+        o.s[LH][0] += sg * ((hhl + hh[0] + 2) >> 2);
+        o.s[LH][1] += sg * ((hh[0] + hh[1] + 2) >> 2);
+      }
+    }
+  }
+};
+
+// ---------------------------------------------------------------------------
+// Type lists and the streaming pipeline
+// ---------------------------------------------------------------------------
+template <class... S>
+struct List {};
+
+template <class A, class B>
+struct Cat;
+template <class... A, class... B>
+struct Cat<List<A...>, List<B...>> {
+  using type = List<A..., B...>;
+};
+
+template <class L>
+struct Totals;
+template <class... S>
+struct Totals<List<S...>> {
+  static constexpr int UP = (0 + ... + S::UP);
+  static constexpr int DOWN = (0 + ... + S::DOWN);
+  static constexpr int LEFT = (0 + ... + S::LEFT);
+  static constexpr int RIGHT = (0 + ... + S::RIGHT);
+};
+
+// A chain of stages; each keeps the rows of its input state it still needs.
+// push() takes the next input row and returns the last stage's output for
+// the row sum(DOWN) positions behind it.
+template <typename V, class L>
+struct Pipe;
+
+template <typename V>
+struct Pipe<V, List<>> {
+  __device__ __forceinline__ void reset() {}
+  __device__ __forceinline__ Row<V> push(const Row<V>& r, const Coefs&, const ConvTaps&) {
+    return r;
+  }
+};
+
+template <typename V, class S0, class... S>
+struct Pipe<V, List<S0, S...>> {
+  static constexpr int NW = S0::UP + 1 + S0::DOWN;
+  Row<V> win[NW];
+  Pipe<V, List<S...>> rest;
+
+  __device__ __forceinline__ void reset() {
+#pragma unroll
+    for (int k = 0; k < NW; ++k)
+#pragma unroll
+      for (int s = 0; s < 4; ++s) win[k].s[s][0] = win[k].s[s][1] = V(0);
+    rest.reset();
+  }
+
+  __device__ __forceinline__ Row<V> push(const Row<V>& r, const Coefs& c, const ConvTaps& t) {
+#pragma unroll
+    for (int k = 0; k + 1 < NW; ++k) win[k] = win[k + 1];
+    win[NW - 1] = r;
+    Row<V> o;
+    S0::eval(win, o, c, t);
+    return rest.push(o, c, t);
+  }
+};
+
+}  // namespace dev
+}  // namespace dwt

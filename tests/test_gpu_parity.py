@@ -1,0 +1,218 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 / exact-int
+oracle, element by element, for every scheme, wavelet and direction, at
+sizes spanning several warp strips with ragged tails, plus edge cases.
+
+Tolerances: float32 max |err| <= 2e-3 against FP64 on 8-bit-range inputs
+(up to 6 levels); reversible integer 5/3 bit-exact; float16 storage has no
+precision bar (its error is printed and sanity-bounded)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1605_00561_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+TOL_F32 = 2e-3
+FLOAT_SCHEMES = ["rowcol", "sweldens", "iwahashi", "iwahashi*", "explosive", "explosive*",
+                 "monolithic", "monolithic*", "polyphase", "polyphase*", "convolution"]
+OID = {"cdf53": oracle.CDF53, "cdf97": oracle.CDF97}
+SHAPES = [(150, 261, 3), (64, 64, 6), (1, 37, 3), (37, 1, 3), (2, 3, 2), (5, 130, 2), (131, 9, 4)]
+
+
+@pytest.fixture(scope="module")
+def dwt():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1605_00561_gb300 import dwt as d
+    d.lib()
+    return d
+
+
+def run_fwd_inv(dwt, x, wavelet, levels, dtype, scheme, coef_in=None):
+    h, w = x.shape
+    plan = dwt.Plan(w, h, wavelet, levels, dtype, scheme=scheme)
+    tdt = {"f32": torch.float32, "f16s": torch.float16, "i32": torch.int32}[dtype]
+    xd = torch.from_numpy(np.ascontiguousarray(x)).to("cuda", tdt)
+    c = torch.empty_like(xd)
+    y = torch.empty_like(xd)
+    plan.forward(xd, c)
+    plan.inverse(c, y)
+    yo = None
+    if coef_in is not None:
+        cd = torch.from_numpy(np.ascontiguousarray(coef_in)).to("cuda", tdt)
+        yo = torch.empty_like(xd)
+        plan.inverse(cd, yo)
+        yo = yo.cpu().numpy()
+    torch.cuda.synchronize()
+    assert dwt.dwt_plan_device_status(plan.handle) == dwt.DWT_OK
+    plan.close()
+    return c.cpu().numpy(), y.cpu().numpy(), yo
+
+
+@pytest.mark.parametrize("scheme", FLOAT_SCHEMES)
+@pytest.mark.parametrize("wavelet", ["cdf53", "cdf97"])
+@pytest.mark.parametrize("h,w,L", SHAPES)
+def test_float32_forward_inverse_vs_oracle(dwt, scheme, wavelet, h, w, L):
+    x = inputs.uniform_image(h, w, seed=h * 1000 + w)
+    ref = oracle.dwt2(x.astype(np.float64), OID[wavelet], L)
+    c, y, yo = run_fwd_inv(dwt, x, wavelet, L, "f32", scheme, coef_in=ref.astype(np.float32))
+    assert np.abs(c - ref).max() <= TOL_F32, "forward"
+    assert np.abs(yo - x).max() <= TOL_F32, "inverse of oracle coefficients"
+    assert np.abs(y - x).max() <= TOL_F32, "round trip"
+
+
+@pytest.mark.parametrize("scheme", ["rowcol", "sweldens"])
+@pytest.mark.parametrize("h,w,L", SHAPES + [(333, 500, 5)])
+def test_int32_bit_exact(dwt, scheme, h, w, L):
+    x = inputs.int12_image(h, w, seed=h + 7 * w)
+    ref = oracle.dwt2_int(x, L)
+    c, y, yo = run_fwd_inv(dwt, x, "cdf53", L, "i32", scheme, coef_in=ref.astype(np.int32))
+    assert np.array_equal(c, ref), "forward"
+    assert np.array_equal(yo, x), "inverse of oracle coefficients"
+    assert np.array_equal(y, x), "round trip"
+
+
+@pytest.mark.parametrize("scheme", FLOAT_SCHEMES)
+@pytest.mark.parametrize("wavelet", ["cdf53", "cdf97"])
+def test_float16_storage_error_reported(dwt, scheme, wavelet):
+    h, w, L = 150, 261, 3
+    x = inputs.uniform_image(h, w, seed=5)
+    ref = oracle.dwt2(x.astype(np.float64), OID[wavelet], L)
+    c, y, _ = run_fwd_inv(dwt, x, wavelet, L, "f16s", scheme)
+    ef = float(np.abs(c.astype(np.float64) - ref).max())
+    er = float(np.abs(y.astype(np.float64) - x).max())
+    print(f"f16s {wavelet} {scheme}: forward max|err| {ef:.3f}, round trip {er:.3f}")
+    assert ef < 2.0 and er < 2.0  # sanity bound, not a precision claim
+
+
+def test_textured_8192_cdf97_six_levels_full_compare(dwt):
+    n, L = 8192, 6
+    x = inputs.textured_image(n, n, seed=2)
+    ref = oracle.dwt2(x.astype(np.float64), oracle.CDF97, L)
+    c, y, _ = run_fwd_inv(dwt, x, "cdf97", L, "f32", "monolithic*")
+    assert np.abs(c - ref).max() <= TOL_F32
+    assert np.abs(y - x).max() <= TOL_F32
+
+
+@pytest.mark.parametrize("h,w", [(4096, 4096), (3333, 5001)])
+def test_int53_config_sizes_bit_exact(dwt, h, w):
+    x = inputs.int12_image(h, w, seed=7)
+    ref = oracle.dwt2_int(x, 5)
+    c, y, _ = run_fwd_inv(dwt, x, "cdf53", 5, "i32", "sweldens")
+    assert np.array_equal(c, ref)
+    assert np.array_equal(y, x)
+
+
+# ---------------------------------------------------------------------------
+# layouts and edge cases
+# ---------------------------------------------------------------------------
+
+def test_pitched_and_unaligned_buffers_with_canaries(dwt):
+    """Unaligned pitch and base (cp.async path instead of TMA); guard bands
+    around the output must stay untouched."""
+    h, w, L = 97, 203, 3
+    x = inputs.uniform_image(h, w, seed=3)
+    ref = oracle.dwt2(x.astype(np.float64), oracle.CDF97, L)
+    big_in = torch.full((h + 4, w + 7), -1.0, device="cuda")
+    big_in[2:2 + h, 3:3 + w] = torch.from_numpy(x).cuda()
+    xin = big_in[2:2 + h, 3:3 + w]
+    big_out = torch.full((h + 4, w + 7), 12345.0, device="cuda")
+    cout = big_out[2:2 + h, 3:3 + w]
+    plan = dwt.Plan(w, h, "cdf97", L, "f32", scheme="monolithic*")
+    plan.forward(xin, cout)
+    torch.cuda.synchronize()
+    got = big_out.cpu().numpy()
+    assert np.abs(got[2:2 + h, 3:3 + w] - ref).max() <= TOL_F32
+    mask = np.ones_like(got, dtype=bool)
+    mask[2:2 + h, 3:3 + w] = False
+    assert np.all(got[mask] == 12345.0)
+    plan.close()
+
+
+def test_levels_zero_is_copy(dwt):
+    x = inputs.uniform_image(33, 17, seed=4)
+    c, y, _ = run_fwd_inv(dwt, x, "cdf97", 0, "f32", None)
+    assert np.array_equal(c, x) and np.array_equal(y, x)
+
+
+def test_invalid_calls_return_status(dwt):
+    plan = dwt.Plan(64, 64, "cdf97", 2, "f32")
+    a = torch.zeros(64, 64, device="cuda")
+    b = torch.zeros(64, 64, device="cuda")
+    host = torch.zeros(64, 64)
+    with pytest.raises(dwt.DwtError) as e:
+        dwt.dwt2_forward(plan.handle, host.data_ptr(), 256, b.data_ptr(), 256)
+    assert e.value.status == dwt.DWT_EINVAL
+    with pytest.raises(dwt.DwtError) as e:
+        dwt.dwt2_forward(plan.handle, a.data_ptr(), 128, b.data_ptr(), 256)  # pitch < row
+    assert e.value.status == dwt.DWT_EINVAL
+    with pytest.raises(dwt.DwtError) as e:
+        dwt.dwt2_forward(plan.handle, a.data_ptr(), 256, a.data_ptr(), 256)  # aliasing
+    assert e.value.status == dwt.DWT_EINVAL
+    small = torch.zeros(32, 64, device="cuda")
+    with pytest.raises(dwt.DwtError) as e:  # buffer shorter than the plane
+        dwt.dwt2_forward(plan.handle, small.data_ptr(), 256, b.data_ptr(), 256)
+    assert e.value.status == dwt.DWT_EINVAL
+    with pytest.raises(dwt.DwtError) as e:
+        dwt.dwt_plan_set_scheme(plan.handle, 99)
+    assert e.value.status == dwt.DWT_EINVAL
+    plan.close()
+    pi = dwt.dwt_plan_create(8, 8, dwt.DWT_CDF53, 1, dwt.DWT_I32)
+    with pytest.raises(dwt.DwtError) as e:
+        dwt.dwt_plan_set_scheme(pi, dwt.SCHEMES["monolithic"])
+    assert e.value.status == dwt.DWT_EUNSUPPORTED
+    dwt.dwt_plan_destroy(pi)
+
+
+def test_two_streams_same_result_as_alone(dwt):
+    h, w, L = 300, 410, 4
+    xs = [inputs.uniform_image(h, w, seed=s) for s in (11, 12)]
+    alone = [run_fwd_inv(dwt, x, "cdf97", L, "f32", "monolithic*")[0] for x in xs]
+    plans = [dwt.Plan(w, h, "cdf97", L, "f32", scheme="monolithic*") for _ in xs]
+    streams = [torch.cuda.Stream() for _ in xs]
+    outs = []
+    for p, s, x in zip(plans, streams, xs):
+        xd = torch.from_numpy(x).cuda()
+        c = torch.empty_like(xd)
+        torch.cuda.synchronize()
+        p.forward(xd, c, stream=s.cuda_stream)
+        outs.append(c)
+    torch.cuda.synchronize()
+    for a, o in zip(alone, outs):
+        assert np.array_equal(a, o.cpu().numpy())
+    for p in plans:
+        p.close()
+
+
+def test_host_buffer_entry_points(dwt):
+    h, w, L = 120, 200, 3
+    x = inputs.uniform_image(h, w, seed=21)
+    ref = oracle.dwt2(x.astype(np.float64), oracle.CDF97, L)
+    plan = dwt.Plan(w, h, "cdf97", L, "f32", scheme="monolithic*")
+    xh = torch.from_numpy(x).pin_memory()
+    ch = torch.empty_like(xh).pin_memory()
+    yh = torch.empty_like(xh).pin_memory()
+    plan.forward_host(xh, ch)
+    plan.inverse_host(ch, yh)
+    torch.cuda.synchronize()
+    assert np.abs(ch.numpy() - ref).max() <= TOL_F32
+    assert np.abs(yh.numpy() - x).max() <= TOL_F32
+    plan.close()
+
+
+def test_profiling_reports_every_level(dwt):
+    h, w, L = 256, 256, 3
+    plan = dwt.Plan(w, h, "cdf97", L, "f32", scheme="monolithic*")
+    dwt.dwt_plan_set_profiling(plan.handle, True)
+    x = torch.rand(h, w, device="cuda")
+    c = torch.empty_like(x)
+    plan.forward(x, c)
+    prof = dwt.dwt_plan_read_profile(plan.handle)
+    names = [p["name"] for p in prof]
+    assert names == ["fwd/L0", "fwd/L1", "fwd/L2"]
+    assert prof[0]["algorithmic_bytes"] == 2 * 256 * 256 * 4
+    assert all(p["total_ms"] > 0 for p in prof)
+    plan.close()
