@@ -52,18 +52,20 @@ using SM = Lin<D, K, false, Term<LL, HL, OP_I, UO, S>, Term<LL, LH, UO, OP_I, S>
                Term<LL, HH, UO, UO, 1>, Term<HL, HH, UO, OP_I, S>, Term<LH, HH, OP_I, UO, S>>;
 
 // --- Polyphase (Sec. 2.3): N_{P,U} with V = PU + 1, and its inverse --------
+// Terms are listed with the same-subband (diagonal) entry of each row last,
+// so that its large contribution is accumulated after the smaller ones.
 template <int D, int K, int PO, int UO, int VO>
 using NP = Lin<D, K, true,
-               Term<LL, LL, VO, VO>, Term<LL, HL, VO, UO>, Term<LL, LH, UO, VO>, Term<LL, HH, UO, UO>,
-               Term<HL, LL, VO, PO>, Term<HL, HL, VO, OP_I>, Term<HL, LH, UO, PO>, Term<HL, HH, UO, OP_I>,
-               Term<LH, LL, PO, VO>, Term<LH, HL, PO, UO>, Term<LH, LH, OP_I, VO>, Term<LH, HH, OP_I, UO>,
+               Term<LL, HL, VO, UO>, Term<LL, LH, UO, VO>, Term<LL, HH, UO, UO>, Term<LL, LL, VO, VO>,
+               Term<HL, LL, VO, PO>, Term<HL, LH, UO, PO>, Term<HL, HH, UO, OP_I>, Term<HL, HL, VO, OP_I>,
+               Term<LH, LL, PO, VO>, Term<LH, HL, PO, UO>, Term<LH, HH, OP_I, UO>, Term<LH, LH, OP_I, VO>,
                Term<HH, LL, PO, PO>, Term<HH, HL, PO, OP_I>, Term<HH, LH, OP_I, PO>, Term<HH, HH, OP_I, OP_I>>;
 // N^{-1} = [[1, -U, -U*, UU*], [-P, V, PU*, -U*V], [-P*, P*U, V*, -UV*], [PP*, -P*V, -PV*, V*V]]
 template <int D, int K, int PO, int UO, int VO>
 using NPinv = Lin<D, K, true,
-               Term<LL, LL, OP_I, OP_I>, Term<LL, HL, OP_I, UO, -1>, Term<LL, LH, UO, OP_I, -1>, Term<LL, HH, UO, UO>,
-               Term<HL, LL, OP_I, PO, -1>, Term<HL, HL, OP_I, VO>, Term<HL, LH, UO, PO>, Term<HL, HH, UO, VO, -1>,
-               Term<LH, LL, PO, OP_I, -1>, Term<LH, HL, PO, UO>, Term<LH, LH, VO, OP_I>, Term<LH, HH, VO, UO, -1>,
+               Term<LL, HL, OP_I, UO, -1>, Term<LL, LH, UO, OP_I, -1>, Term<LL, HH, UO, UO>, Term<LL, LL, OP_I, OP_I>,
+               Term<HL, LL, OP_I, PO, -1>, Term<HL, LH, UO, PO>, Term<HL, HH, UO, VO, -1>, Term<HL, HL, OP_I, VO>,
+               Term<LH, LL, PO, OP_I, -1>, Term<LH, HL, PO, UO>, Term<LH, HH, VO, UO, -1>, Term<LH, LH, VO, OP_I>,
                Term<HH, LL, PO, PO>, Term<HH, HL, PO, VO, -1>, Term<HH, LH, VO, PO, -1>, Term<HH, HH, VO, VO>>;
 
 // ---------------------------------------------------------------------------

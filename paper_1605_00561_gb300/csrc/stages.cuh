@@ -140,7 +140,10 @@ struct Lin {
   static constexpr int RIGHT = vmax(0, OpShape<DEG, Ts::hop>::hi...);
   static constexpr unsigned TARGETS = (0u | ... | (1u << Ts::tgt));
 
-  template <class T>
+  // One term, off-centre taps first and the centre tap last: the centre
+  // carries the largest coefficient of the products V*V, V*P, ..., and adding
+  // it last keeps the rounding of the partial sums small.
+  template <class T, bool CENTRE>
   __device__ __forceinline__ static void term(const Row<float>* w, Row<float>& o, const Coefs& c) {
     using VS = OpShape<DEG, T::vop>;
     using HS = OpShape<DEG, T::hop>;
@@ -150,7 +153,7 @@ struct Lin {
         const float(&x)[2] = w[UP + DY].s[T::src];
         static_for<HS::lo, HS::hi>([&](auto dx) {
           constexpr int DX = decltype(dx)::value;
-          if constexpr (HS::has(DX)) {
+          if constexpr (HS::has(DX) && ((DY == 0 && DX == 0) == CENTRE)) {
             const float cf = (T::sgn > 0 ? 1.0f : -1.0f) * op_tap<DEG, T::vop, K, 0, DY>(c) *
                              op_tap<DEG, T::hop, K, 1, DX>(c);
             o.s[T::tgt][0] = fmaf(cf, hpos<0 + DX>(x), o.s[T::tgt][0]);
@@ -169,7 +172,8 @@ struct Lin {
       for (int s = 0; s < 4; ++s)
         if (TARGETS & (1u << s)) o.s[s][0] = o.s[s][1] = 0.0f;
     }
-    (term<Ts>(w, o, c), ...);
+    (term<Ts, false>(w, o, c), ...);
+    (term<Ts, true>(w, o, c), ...);
   }
 };
 
