@@ -329,7 +329,7 @@ struct dwt_plan_s {
   std::vector<ProfSlot> slots;
   std::vector<ProfRec> pending;
   std::vector<cudaEvent_t> pool;
-  int nstages = 4;
+  int nstages = kDefaultStages;
   int tmin = 8;
   std::mutex mu;
 };
@@ -742,6 +742,15 @@ dwt_status dwt_plan_set_scheme(dwt_plan p, dwt_scheme scheme) {
     DeviceGuard g(p->device);
     return ensure_tmp(p);
   }
+  return DWT_OK;
+}
+
+dwt_status dwt_plan_set_tile(dwt_plan p, int min_strip_rows, int stages) {
+  if (!p || min_strip_rows < 0 || min_strip_rows > 1 << 20 || stages < 0 || stages > kMaxStages)
+    return DWT_EINVAL;
+  std::lock_guard<std::mutex> lk(p->mu);
+  p->tmin = min_strip_rows ? min_strip_rows : 8;
+  p->nstages = stages ? stages : kDefaultStages;
   return DWT_OK;
 }
 

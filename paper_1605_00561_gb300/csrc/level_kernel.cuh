@@ -75,7 +75,11 @@ struct Cfg {
 };
 
 __device__ __forceinline__ int mirror(int i, int n) {
-  // whole-sample symmetric extension, period 2(n - 1); n >= 2
+  // whole-sample symmetric extension (n >= 2): one reflection covers every
+  // index within n - 1 of the line; shorter lines fold with period 2(n - 1)
+  if (i < 0) i = -i;
+  if (i >= n) i = 2 * (n - 1) - i;
+  if ((unsigned)i < (unsigned)n) return i;
   const int period = 2 * (n - 1);
   i %= period;
   if (i < 0) i += period;
@@ -173,25 +177,39 @@ struct Strip {
         return;
       }
       const bool async = !tiny && C::ES == 4;
+      const int m = mfirst + 2 * lane;
 #pragma unroll
       for (int p = 0; p < 4; ++p) {
         const int py = p >> 1, px = p & 1;
         const int pw = px ? a.fw : a.cw, ph = py ? a.fh : a.ch;
         ST* pd = reinterpret_cast<ST*>(reinterpret_cast<unsigned char*>(dst) + p * C::PLANE_BYTES);
+        if (async) {
+          // mirroring keeps the parity of a sample index, so a mirrored
+          // element of plane p is again in plane p
+          int ix[2];
+#pragma unroll
+          for (int t = 0; t < 2; ++t) {
+            const int mm = m + t;
+            ix[t] = (mm >= 0 && mm < pw) ? mm : (mirror(2 * mm + px, a.W) >> 1);
+          }
+          const bool direct = m >= 0 && m + 2 <= pw;
+          for (int r = 0; r < C::CH; ++r) {
+            const int y = y0 + r;
+            const int iy = (y >= 0 && y < ph) ? y : (mirror(2 * y + py, a.H) >> 1);
+            const ST* rowp = src_plane(p) + (long long)iy * a.src_pitch[p];
+            ST* d = pd + r * C::ROWE + off + 2 * lane;
+            if (direct && (reinterpret_cast<uintptr_t>(rowp + m) & 7) == 0) {
+              ptx::cp_async_8(d, rowp + m);
+            } else {
+              ptx::cp_async_4(d, rowp + ix[0]);
+              ptx::cp_async_4(d + 1, rowp + ix[1]);
+            }
+          }
+          continue;
+        }
         for (int r = 0; r < C::CH; ++r) {
           const int y = y0 + r;
           ST* d = pd + r * C::ROWE + off + 2 * lane;
-          const int m = mfirst + 2 * lane;
-          if (async && y >= 0 && y < ph && m >= 0 && m + 2 <= pw) {
-            const ST* sp = src_plane(p) + (long long)y * a.src_pitch[p] + m;
-            if ((reinterpret_cast<uintptr_t>(sp) & 7) == 0) {
-              ptx::cp_async_8(d, sp);
-            } else {
-              ptx::cp_async_4(d, sp);
-              ptx::cp_async_4(d + 1, sp + 1);
-            }
-            continue;
-          }
 #pragma unroll
           for (int t = 0; t < 2; ++t) {
             // sample coordinates of this element, mirrored, mapped back to a plane
@@ -202,11 +220,7 @@ struct Strip {
             if (a.W == 1) { mx = 0; absent |= sx != 0; } else { mx = mirror(sx, a.W); }
             const int q = ((my & 1) << 1) | (mx & 1);
             const ST* sp = src_plane(q) + (long long)(my >> 1) * a.src_pitch[q] + (mx >> 1);
-            if (async) {
-              ptx::cp_async_4(d + t, sp);
-            } else {
-              d[t] = absent ? StoreT<ST>::from_v(VT(0)) : *sp;
-            }
+            d[t] = absent ? StoreT<ST>::from_v(VT(0)) : *sp;
           }
         }
       }
@@ -259,18 +273,55 @@ struct Strip {
     return o;
   }
 
-  __device__ __forceinline__ void store_row(const Row<VT>& r, int q) const {
+  // Per-lane output bases, computed once per strip.
+  struct Out {
+    ST* base[4];
+    long long pitch[4];
+    int rows[4];
+    bool pair[4];   // both quads stored with one vector access
+    bool one[2];    // quad a / quad b stored (SUBBANDS) or sample columns (SAMPLES)
+    bool lane_ok;
+  };
+
+  __device__ __forceinline__ Out out_bases() const {
+    Out o;
     const int m = mfirst + 2 * lane;
-    if (m < m0 || m >= m0 + C::UQ) return;  // halo lane
+    o.lane_ok = m >= m0 && m < m0 + C::UQ;
     if constexpr (C::STORE == SUBBANDS) {
 #pragma unroll
       for (int p = 0; p < 4; ++p) {
-        const int ph = (p >> 1) ? a.fh : a.ch;
         const int pw = (p & 1) ? a.fw : a.cw;
-        if (q >= ph) continue;
-        ST* rowp = static_cast<ST*>(a.dst[p]) + (long long)q * a.dst_pitch[p] + m;
+        o.rows[p] = (p >> 1) ? a.fh : a.ch;
+        o.base[p] = static_cast<ST*>(a.dst[p]) + m;
+        o.pitch[p] = a.dst_pitch[p];
+        o.pair[p] = m + 2 <= pw && ((reinterpret_cast<uintptr_t>(o.base[p]) & (2 * C::ES - 1)) == 0) &&
+                    ((a.dst_pitch[p] * C::ES) & (2 * C::ES - 1)) == 0;
+        if (p == 0) {
+          o.one[0] = m < pw;
+          o.one[1] = m + 1 < pw;
+        }
+      }
+    } else {
+      const int gx = 2 * m;
+      o.base[0] = static_cast<ST*>(a.dst[0]) + gx;
+      o.pitch[0] = a.dst_pitch[0];
+      o.rows[0] = a.H;
+      o.pair[0] = gx + 4 <= a.W && ((reinterpret_cast<uintptr_t>(o.base[0]) & (4 * C::ES - 1)) == 0) &&
+                  ((a.dst_pitch[0] * C::ES) & (4 * C::ES - 1)) == 0;
+    }
+    return o;
+  }
+
+  __device__ __forceinline__ void store_row(const Out& o, const Row<VT>& r, int q) const {
+    if (!o.lane_ok) return;  // halo lane
+    if constexpr (C::STORE == SUBBANDS) {
+      const int m = mfirst + 2 * lane;
+#pragma unroll
+      for (int p = 0; p < 4; ++p) {
+        if (q >= o.rows[p]) continue;
+        ST* rowp = o.base[p] + (long long)q * o.pitch[p];
         const ST v0 = StoreT<ST>::from_v(r.s[p][0]), v1 = StoreT<ST>::from_v(r.s[p][1]);
-        if (m + 2 <= pw && (reinterpret_cast<uintptr_t>(rowp) & (2 * C::ES - 1)) == 0) {
+        if (o.pair[p]) {
           if constexpr (C::ES == 4) {
             int2 pk;
             pk.x = *reinterpret_cast<const int*>(&v0);
@@ -283,21 +334,22 @@ struct Strip {
             *reinterpret_cast<__half2*>(rowp) = h;
           }
         } else {
+          const int pw = (p & 1) ? a.fw : a.cw;
           if (m < pw) rowp[0] = v0;
           if (m + 1 < pw) rowp[1] = v1;
         }
       }
     } else {
-      const int gx = 2 * m;
+      const int gx = 2 * (mfirst + 2 * lane);
 #pragma unroll
       for (int rr = 0; rr < 2; ++rr) {
         const int gy = 2 * q + rr;
-        if (gy >= a.H) continue;
-        ST* rowp = static_cast<ST*>(a.dst[0]) + (long long)gy * a.dst_pitch[0] + gx;
+        if (gy >= o.rows[0]) continue;
+        ST* rowp = o.base[0] + (long long)gy * o.pitch[0];
         const int sl = rr ? LH : LL, sh = rr ? HH : HL;
         ST v[4] = {StoreT<ST>::from_v(r.s[sl][0]), StoreT<ST>::from_v(r.s[sh][0]),
                    StoreT<ST>::from_v(r.s[sl][1]), StoreT<ST>::from_v(r.s[sh][1])};
-        if (gx + 4 <= a.W && (reinterpret_cast<uintptr_t>(rowp) & (4 * C::ES - 1)) == 0) {
+        if (o.pair[0]) {
           if constexpr (C::ES == 4) *reinterpret_cast<int4*>(rowp) = *reinterpret_cast<const int4*>(v);
           else *reinterpret_cast<int2*>(rowp) = *reinterpret_cast<const int2*>(v);
         } else {
@@ -334,10 +386,14 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32)
   }
   __syncwarp();
 
+  // rows streamed: the strip plus its halo, padded to whole chunks (the
+  // extra rows are mirrored image rows, lifted but never stored)
   const int nrows = rows_out + Tot::UP + Tot::DOWN;
   const int nchunks = (nrows + C::CH - 1) / C::CH;
+  const int q_end = q0 + rows_out;
   for (int c = 0; c < NS - 1 && c < nchunks; ++c) sp.fill(c, c);
 
+  const typename Strip<C>::Out ob = sp.out_bases();
   Pipe<typename C::VT, typename C::PROG> pipe;
   pipe.reset();
   for (int c = 0; c < nchunks; ++c) {
@@ -358,15 +414,13 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32)
       return;
     }
     const typename C::ST* st = sp.stage(s);
+    const int qc = sp.yfirst + c * C::CH - Tot::DOWN;
 #pragma unroll
     for (int r = 0; r < C::CH; ++r) {
-      const int i = c * C::CH + r;
-      if (i < nrows) {
-        const Row<typename C::VT> in = sp.load_row(st, r);
-        const Row<typename C::VT> out = pipe.push(in, cf, ct);
-        const int q = sp.yfirst + i - Tot::DOWN;
-        if (q >= q0) sp.store_row(out, q);
-      }
+      const Row<typename C::VT> in = sp.load_row(st, r);
+      const Row<typename C::VT> out = pipe.push(in, cf, ct);
+      const int q = qc + r;
+      if (q >= q0 && q < q_end) sp.store_row(ob, out, q);
     }
   }
 }

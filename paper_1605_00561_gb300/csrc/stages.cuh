@@ -95,6 +95,25 @@ struct OpShape {
   __host__ __device__ static constexpr bool has(int off) {
     return !((OP == OP_P1 || OP == OP_U1) && DEG == 3 && off == 0);
   }
+  // Taps with equal coefficients form a class: P and U have one class of
+  // two taps (degree 1) or two classes (degree 3: distance 1 and 3); V has
+  // its centre 1 + 2pu and the pair pu.  Class 0 holds the centre tap when
+  // the operator has one.
+  __host__ __device__ static constexpr int cls(int off) {
+    return OP == OP_V ? (off == 0 ? 0 : 1)
+           : (DEG == 3 && (OP == OP_P || OP == OP_P1)) ? ((off == 0 || off == 1) ? 0 : 1)
+           : (DEG == 3 && (OP == OP_U || OP == OP_U1)) ? ((off == -1 || off == 0) ? 0 : 1)
+                                                       : 0;
+  }
+  static constexpr int NCLS = (OP == OP_V || (DEG == 3 && (OP == OP_P || OP == OP_P1 ||
+                                                           OP == OP_U || OP == OP_U1))) ? 2 : 1;
+  // a representative offset of each class (for its coefficient)
+  __host__ __device__ static constexpr int rep(int c) {
+    return OP == OP_V ? (c == 0 ? 0 : 1)
+           : (DEG == 3 && (OP == OP_P || OP == OP_P1)) ? (c == 0 ? 1 : 2)
+           : (DEG == 3 && (OP == OP_U || OP == OP_U1)) ? (c == 0 ? -1 : 1)
+                                                       : lo;
+  }
 };
 
 // Coefficient of operator OP (pair K, axis: 0 vertical, 1 horizontal) at
@@ -140,27 +159,50 @@ struct Lin {
   static constexpr int RIGHT = vmax(0, OpShape<DEG, Ts::hop>::hi...);
   static constexpr unsigned TARGETS = (0u | ... | (1u << Ts::tgt));
 
-  // One term, off-centre taps first and the centre tap last: the centre
-  // carries the largest coefficient of the products V*V, V*P, ..., and adding
-  // it last keeps the rounding of the partial sums small.
-  template <class T, bool CENTRE>
+  // One term.  Taps of equal coefficient are summed first and multiplied
+  // once (P x = p (x0 + x1), P P* x = p^2 (sum of four), ...): fewer
+  // roundings at the magnitude of the target than one FMA per tap.  The
+  // class holding the centre tap, whose coefficient is the largest in the
+  // products of V, is accumulated in the second pass, after all others.
+  template <class T, bool CENTRE_PASS>
   __device__ __forceinline__ static void term(const Row<float>* w, Row<float>& o, const Coefs& c) {
     using VS = OpShape<DEG, T::vop>;
     using HS = OpShape<DEG, T::hop>;
-    static_for<VS::lo, VS::hi>([&](auto dy) {
-      constexpr int DY = decltype(dy)::value;
-      if constexpr (VS::has(DY)) {
-        const float(&x)[2] = w[UP + DY].s[T::src];
-        static_for<HS::lo, HS::hi>([&](auto dx) {
-          constexpr int DX = decltype(dx)::value;
-          if constexpr (HS::has(DX) && ((DY == 0 && DX == 0) == CENTRE)) {
-            const float cf = (T::sgn > 0 ? 1.0f : -1.0f) * op_tap<DEG, T::vop, K, 0, DY>(c) *
-                             op_tap<DEG, T::hop, K, 1, DX>(c);
-            o.s[T::tgt][0] = fmaf(cf, hpos<0 + DX>(x), o.s[T::tgt][0]);
-            o.s[T::tgt][1] = fmaf(cf, hpos<1 + DX>(x), o.s[T::tgt][1]);
-          }
-        });
-      }
+    static_for<0, VS::NCLS - 1>([&](auto cvi) {
+      constexpr int CV = decltype(cvi)::value;
+      static_for<0, HS::NCLS - 1>([&](auto chi) {
+        constexpr int CH = decltype(chi)::value;
+        constexpr bool centre = VS::has(0) && HS::has(0) && VS::cls(0) == CV && HS::cls(0) == CH &&
+                                VS::lo <= 0 && VS::hi >= 0 && HS::lo <= 0 && HS::hi >= 0;
+        if constexpr (centre == CENTRE_PASS) {
+          float s0 = 0.0f, s1 = 0.0f;
+          bool first = true;
+          static_for<VS::lo, VS::hi>([&](auto dy) {
+            constexpr int DY = decltype(dy)::value;
+            if constexpr (VS::has(DY) && VS::cls(DY) == CV) {
+              const float(&x)[2] = w[UP + DY].s[T::src];
+              static_for<HS::lo, HS::hi>([&](auto dx) {
+                constexpr int DX = decltype(dx)::value;
+                if constexpr (HS::has(DX) && HS::cls(DX) == CH) {
+                  const float a0 = hpos<0 + DX>(x), a1 = hpos<1 + DX>(x);
+                  if (first) {
+                    s0 = a0;
+                    s1 = a1;
+                    first = false;
+                  } else {
+                    s0 += a0;
+                    s1 += a1;
+                  }
+                }
+              });
+            }
+          });
+          const float cf = (T::sgn > 0 ? 1.0f : -1.0f) * op_tap<DEG, T::vop, K, 0, VS::rep(CV)>(c) *
+                           op_tap<DEG, T::hop, K, 1, HS::rep(CH)>(c);
+          o.s[T::tgt][0] = fmaf(cf, s0, o.s[T::tgt][0]);
+          o.s[T::tgt][1] = fmaf(cf, s1, o.s[T::tgt][1]);
+        }
+      });
     });
   }
 

@@ -17,7 +17,7 @@ __all__ = [
     "DWT_OK", "DWT_EINVAL", "DWT_ENOMEM", "DWT_EUNSUPPORTED", "DWT_ECUDA", "DWT_ETIMEOUT", "DWT_EBUSY",
     "DWT_CDF53", "DWT_CDF97", "DWT_DD137", "DWT_F32", "DWT_F16S", "DWT_I32",
     "SCHEMES", "DWT_NORM_JPEG2000", "DWT_NORM_ZETA",
-    "dwt_plan_create", "dwt_plan_set_scheme", "dwt_plan_get_scheme", "dwt_plan_set_normalization",
+    "dwt_plan_create", "dwt_plan_set_scheme", "dwt_plan_set_tile", "dwt_plan_get_scheme", "dwt_plan_set_normalization",
     "dwt2_forward", "dwt2_inverse", "dwt2_forward_host", "dwt2_inverse_host", "dwt_batch_submit",
     "dwt_plan_device_status", "dwt_plan_set_profiling", "dwt_plan_read_profile", "dwt_plan_autotune",
     "dwt_plan_destroy", "dwt_status_string", "dwt_version", "Plan", "DwtRequest",
@@ -59,6 +59,7 @@ EXPORTS = {
                          ctypes.POINTER(ctypes.c_void_p)], ctypes.c_int),
     "dwt_plan_set_scheme": ([ctypes.c_void_p, ctypes.c_int], ctypes.c_int),
     "dwt_plan_get_scheme": ([ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
+    "dwt_plan_set_tile": ([ctypes.c_void_p, ctypes.c_int, ctypes.c_int], ctypes.c_int),
     "dwt_plan_set_normalization": ([ctypes.c_void_p, ctypes.c_int], ctypes.c_int),
     "dwt2_forward": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_size_t,
                       ctypes.c_void_p], ctypes.c_int),
@@ -119,6 +120,10 @@ def dwt_plan_create(w: int, h: int, wavelet: int, levels: int, dtype: int) -> in
 
 def dwt_plan_set_scheme(plan: int, scheme: int) -> None:
     _check(lib().dwt_plan_set_scheme(plan, scheme), "dwt_plan_set_scheme")
+
+
+def dwt_plan_set_tile(plan: int, min_strip_rows: int = 0, stages: int = 0) -> None:
+    _check(lib().dwt_plan_set_tile(plan, min_strip_rows, stages), "dwt_plan_set_tile")
 
 
 def dwt_plan_get_scheme(plan: int) -> int:
