@@ -33,7 +33,7 @@ enum Pass : int {
 constexpr int kWarpsPerCta = 4;  // independent warps (one strip each) per CTA
 constexpr int kChunkRows = 4;    // quad rows per pipeline stage
 constexpr int kMaxStages = 4;    // ring depth per warp
-constexpr int kDefaultStages = 3;
+constexpr int kDefaultStages = 2;
 
 // Lifting coefficients per predict/update pair and axis.  A coefficient of
 // an axis whose length is 1 is zero, which makes that axis' lifting the

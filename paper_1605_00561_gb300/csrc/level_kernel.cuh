@@ -415,7 +415,9 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32)
     }
     const typename C::ST* st = sp.stage(s);
     const int qc = sp.yfirst + c * C::CH - Tot::DOWN;
-#pragma unroll
+    // unrolled by two rows: the stage windows rotate with period two, and
+    // the loop body stays small enough for the instruction cache
+#pragma unroll 2
     for (int r = 0; r < C::CH; ++r) {
       const Row<typename C::VT> in = sp.load_row(st, r);
       const Row<typename C::VT> out = pipe.push(in, cf, ct);
