@@ -17,9 +17,23 @@ inline bool run(int nstages, KernelInfo* info, const LaunchCall* call, cudaError
   return true;
 }
 
+// Quadruples per lane: four for the light schemes (128-bit vectors, fewer
+// instructions per pixel); two for the schemes whose windows or stencils
+// would otherwise exceed the register file (Polyphase, Convolution, and the
+// three-step schemes of two pairs).  A ring stage holds the same bytes
+// either way.
+template <int SCHEME, int WL>
+constexpr int kQuadsPerLane =
+    (SCHEME == POLYPHASE || SCHEME == POLYPHASE_S || SCHEME == CONVOLUTION ||
+     (WL == W97 && (SCHEME == IWAHASHI || SCHEME == IWAHASHI_S || SCHEME == EXPLOSIVE ||
+                    SCHEME == EXPLOSIVE_S)))
+        ? 2
+        : 4;
+
 template <int SCHEME, int WL, typename ST, bool INV>
 using FusedCfg = Cfg<ST, float, typename FusedProgram<SCHEME, WL, INV>::type, INV ? SUBBANDS : SAMPLES,
-                     INV ? SAMPLES : SUBBANDS>;
+                     INV ? SAMPLES : SUBBANDS, kQuadsPerLane<SCHEME, WL>, 8 / kQuadsPerLane<SCHEME, WL>,
+                     SCHEME == CONVOLUTION ? 2 : 4>;
 
 // The eight float combinations of one fused scheme.
 template <int SCHEME>

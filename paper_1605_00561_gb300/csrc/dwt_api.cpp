@@ -462,9 +462,10 @@ dwt_status launch(dwt_plan_s* p, const LaunchKey& key, LevelArgs& a, const Coefs
   if (!find_kernel(key, p->nstages, &ki)) return DWT_EUNSUPPORTED;
   const Occ oc = occupancy(ki, p->device);
   const int cap = oc.sms * oc.per_sm;
+  // one strip per resident warp when the level is large enough: a single
+  // wave, with strips as tall as that allows (less vertical halo)
   a.ncs = (a.cw + ki.uq - 1) / ki.uq;
-  const int ctas_row = (a.ncs + kWarpsPerCta - 1) / kWarpsPerCta;
-  const int nrs_target = std::max(1, cap / ctas_row);
+  const int nrs_target = std::max(1, cap * kWarpsPerCta / a.ncs);
   a.T = std::max(p->tmin, (a.ch + nrs_target - 1) / nrs_target);
   a.nrs = (a.ch + a.T - 1) / a.T;
   a.nstages = p->nstages;

@@ -31,7 +31,6 @@ enum Pass : int {
 };
 
 constexpr int kWarpsPerCta = 4;  // independent warps (one strip each) per CTA
-constexpr int kChunkRows = 4;    // quad rows per pipeline stage
 constexpr int kMaxStages = 4;    // ring depth per warp
 constexpr int kDefaultStages = 2;
 
@@ -60,7 +59,7 @@ struct LevelArgs {
   int cw, ch;  // ceil(W/2), ceil(H/2): quads / LL size
   int fw, fh;  // floor(W/2), floor(H/2)
   // Strips: column strip cs covers useful quads [cs*UQ, cs*UQ+UQ); row
-  // strip rs covers quad rows [rs*T, rs*T+T).
+  // strip rs covers quad rows [rs*T, rs*T+T); strip index rs*ncs + cs.
   int ncs, nrs, T;
   int nstages;  // ring depth used (<= kMaxStages)
   // Sources and destinations (element pitches).

@@ -1,7 +1,7 @@
 // One transform level (or one row-column pass) as a streaming kernel.
 //
-// Work decomposition.  Each warp owns a strip: 64 quadruple columns wide
-// (two per lane) and T quadruple rows tall.  The outer HQ quad columns on
+// Work decomposition.  Each warp owns a strip: 32*QL quadruple columns wide
+// (QL per lane) and T quadruple rows tall.  The outer HQ quad columns on
 // each side and UP / DOWN quad rows are the lifting halo (the overlapping
 // tiles of Sec. 6): they are loaded and lifted but not stored, so that every
 // stored coefficient only depends on samples the strip holds.  The warp
@@ -11,17 +11,22 @@
 // warp shuffles.  What the paper synchronises with a work-group barrier
 // between two steps is, here, the hand-over of a row from one stage's
 // output to the next stage's window (vertical) and a shuffle (horizontal);
-// no CTA-wide barrier is needed.
+// no CTA-wide barrier is needed.  Strips are numbered row-major over the
+// level and four consecutive strips form a CTA, so every CTA is full.
 //
-// Loads.  Rows arrive in chunks of kChunkRows quad rows through a per-warp
-// ring of shared-memory stages, filled ahead of use: a chunk lying inside
-// the image is one 2-D TMA box (cp.async.bulk.tensor, one box per source
-// plane) when the source is 16-byte aligned; otherwise each lane issues
-// cp.async copies, with whole-sample symmetric mirroring applied to the
-// addresses at the image border.  Images with a length-1 axis use a
-// synchronous fill that writes zeros for the samples that do not exist.
-// Every stage has one mbarrier with 32 expected arrivals per fill; waits on
-// it are bounded and report to the launch's status word.
+// Loads.  Rows arrive in chunks of CH quad rows through a per-warp ring of
+// shared-memory stages, filled ahead of use: a chunk lying inside the image
+// is one 2-D TMA box (cp.async.bulk.tensor, one box per source plane) when
+// the source is 16-byte aligned; otherwise each lane issues cp.async copies,
+// with whole-sample symmetric mirroring applied to the addresses at the
+// image border.  Images with a length-1 axis use a synchronous fill that
+// writes zeros for the samples that do not exist.  Every stage has one
+// mbarrier with 32 expected arrivals per fill; waits on it are bounded and
+// report to the launch's status word.
+//
+// Stores.  Each lane writes its QL quadruples of a subband row as one vector
+// (128-bit for float32 and QL = 4) or, for sample output, its 2*QL samples
+// of each sample row.
 #pragma once
 
 #include <cuda_fp16.h>
@@ -52,26 +57,53 @@ struct StoreT<int> {
   __device__ __forceinline__ static int from_v(int x) { return x; }
 };
 
-template <typename ST_, typename VT_, class PROG_, int LOAD_, int STORE_>
+// Copies of N bytes (N a power of two, 4..32) between aligned addresses.
+template <int N>
+__device__ __forceinline__ void copy_bytes(void* d, const void* s) {
+  if constexpr (N == 32) {
+    reinterpret_cast<int4*>(d)[0] = reinterpret_cast<const int4*>(s)[0];
+    reinterpret_cast<int4*>(d)[1] = reinterpret_cast<const int4*>(s)[1];
+  } else if constexpr (N == 16) {
+    *reinterpret_cast<int4*>(d) = *reinterpret_cast<const int4*>(s);
+  } else if constexpr (N == 8) {
+    *reinterpret_cast<int2*>(d) = *reinterpret_cast<const int2*>(s);
+  } else {
+    static_assert(N == 4, "unsupported copy size");
+    *reinterpret_cast<int*>(d) = *reinterpret_cast<const int*>(s);
+  }
+}
+
+template <typename ST_, typename VT_, class PROG_, int LOAD_, int STORE_, int QL_ = 4, int CH_ = 2,
+          int MINB_ = 4>
 struct Cfg {
   using ST = ST_;
   using VT = VT_;
   using PROG = PROG_;
   using Tot = Totals<PROG>;
   static constexpr int LOAD = LOAD_, STORE = STORE_;
-  static constexpr int HQ = ((cmax(Tot::LEFT, Tot::RIGHT) + 1) / 2) * 2;
-  static constexpr int UQ = 64 - 2 * HQ;
+  static constexpr int QL = QL_;  // quadruples per lane
+  static constexpr int CH = CH_;  // quad rows per ring stage
+  static constexpr int MIN_BLOCKS = MINB_;  // CTAs per SM the register budget must allow
+  static constexpr int WQ = 32 * QL;  // quadruple columns per warp
+  // halo quads per side: covers the stencil reach and keeps each lane's
+  // first quadruple a multiple of QL (aligned vector stores)
+  static constexpr int HQ = ((cmax(Tot::LEFT, Tot::RIGHT) + QL - 1) / QL) * QL;
+  static constexpr int UQ = WQ - 2 * HQ;
   static constexpr int ES = sizeof(ST);
   static constexpr int A = 16 / ES;  // elements per 16 bytes
-  static constexpr int CH = kChunkRows;
-  static constexpr int ROWE = (LOAD == SAMPLES ? 128 : 64) + A;
-  // bytes of one plane's box; planes start on 128-byte boundaries
-  static constexpr int PLANE_BYTES =
-      LOAD == SAMPLES ? 2 * CH * ROWE * ES : ((CH * ROWE * ES + 127) / 128) * 128;
-  static constexpr int BOX_BYTES = LOAD == SAMPLES ? 2 * CH * ROWE * ES : CH * ROWE * ES;
+  // smem row: the warp's span plus alignment slack when the box start can
+  // be misaligned (a TMA box is at most 256 elements wide)
+  static constexpr int SPAN = LOAD == SAMPLES ? 2 * WQ : WQ;
+  static constexpr bool ALIGNED_START = LOAD == SAMPLES ? ((2 * HQ) % A == 0 && (2 * UQ) % A == 0)
+                                                        : (HQ % A == 0 && UQ % A == 0);
+  static constexpr int ROWE = ALIGNED_START ? SPAN : SPAN + A;
+  static constexpr int ROWS = LOAD == SAMPLES ? 2 * CH : CH;  // smem rows per plane
+  static constexpr int PLANE_BYTES = ((ROWS * ROWE * ES + 127) / 128) * 128;
+  static constexpr int BOX_BYTES = ROWS * ROWE * ES;
   static constexpr int NPLANES = LOAD == SAMPLES ? 1 : 4;
-  static constexpr int STAGE_BYTES = ((NPLANES * PLANE_BYTES + 127) / 128) * 128;
-  static_assert(HQ <= 8, "halo too wide for a 64-quad strip");
+  static constexpr int STAGE_BYTES = NPLANES * PLANE_BYTES;
+  static_assert(ROWE <= 256, "TMA box wider than 256 elements");
+  static_assert(UQ > 0 && HQ <= 2 * QL, "halo too wide for the lane layout");
 };
 
 __device__ __forceinline__ int mirror(int i, int n) {
@@ -94,34 +126,43 @@ template <class C>
 struct Strip {
   using ST = typename C::ST;
   using VT = typename C::VT;
+  static constexpr int QL = C::QL;
   const LevelArgs& a;
   const TmaMaps& maps;
   int lane, m0, mfirst, yfirst;
   unsigned char* sm;
   uint64_t* bars;
 
-  __device__ __forceinline__ ST* stage(int s) const {
-    return reinterpret_cast<ST*>(sm + (size_t)s * C::STAGE_BYTES);
+  __device__ __forceinline__ ST* plane(int s, int p) const {
+    return reinterpret_cast<ST*>(sm + (size_t)s * C::STAGE_BYTES + p * C::PLANE_BYTES);
   }
   __device__ __forceinline__ const ST* src_plane(int p) const {
     return static_cast<const ST*>(a.src[p]);
+  }
+  // first smem column of the lane's elements
+  __device__ __forceinline__ int lane_col() const {
+    if constexpr (C::LOAD == SAMPLES) {
+      const int xs = 2 * mfirst;
+      return (xs - align_down(xs, C::A)) + 2 * QL * lane;
+    } else {
+      return (mfirst - align_down(mfirst, C::A)) + QL * lane;
+    }
   }
 
   // ---- fills ---------------------------------------------------------------
   __device__ void fill(int c, int s) const {
     const int y0 = yfirst + c * C::CH;
     uint64_t* bar = &bars[s];
-    ST* dst = stage(s);
     const bool tiny = a.W < 2 || a.H < 2;
+    const int col = lane_col();
     if constexpr (C::LOAD == SAMPLES) {
       const int sy0 = 2 * y0, xs = 2 * mfirst;
-      const int xal = align_down(xs, C::A), off = xs - xal;
-      const bool inside = !tiny && sy0 >= 0 && sy0 + 2 * C::CH <= a.H && xs >= 0 && xs + 128 <= a.W;
+      const bool inside = !tiny && sy0 >= 0 && sy0 + C::ROWS <= a.H && xs >= 0 && xs + C::SPAN <= a.W;
       if (inside && a.src_tma) {
         if (lane == 0) {
           ptx::fence_proxy_async_smem();
           ptx::mbar_arrive_expect_tx(bar, C::BOX_BYTES);
-          ptx::tma_load_2d(dst, &maps.m[0], xal, sy0, bar);
+          ptx::tma_load_2d(plane(s, 0), &maps.m[0], align_down(xs, C::A), sy0, bar);
         } else {
           ptx::mbar_arrive(bar);
         }
@@ -129,89 +170,91 @@ struct Strip {
       }
       const ST* src = src_plane(0);
       const long long pitch = a.src_pitch[0];
+      const int gx = xs + 2 * QL * lane;
       if (!tiny && C::ES == 4) {
-        for (int j = 0; j < 2 * C::CH; ++j) {
+        int ix[2 * QL];
+#pragma unroll
+        for (int t = 0; t < 2 * QL; ++t) ix[t] = mirror(gx + t, a.W);
+        const bool direct = gx >= 0 && gx + 2 * QL <= a.W;
+        for (int j = 0; j < C::ROWS; ++j) {
           const ST* rowp = src + (long long)mirror(sy0 + j, a.H) * pitch;
-          ST* d = dst + j * C::ROWE + off + 4 * lane;
-          const int gx = xs + 4 * lane;
-          if (gx >= 0 && gx + 4 <= a.W && ((reinterpret_cast<uintptr_t>(rowp + gx) & 15) == 0)) {
-            ptx::cp_async_16(d, rowp + gx);
+          ST* d = plane(s, 0) + j * C::ROWE + col;
+          if (direct && ((reinterpret_cast<uintptr_t>(rowp + gx) & 15) == 0)) {
+#pragma unroll
+            for (int t = 0; t < 2 * QL; t += 4) ptx::cp_async_16(d + t, rowp + gx + t);
           } else {
 #pragma unroll
-            for (int t = 0; t < 4; ++t) ptx::cp_async_4(d + t, rowp + mirror(gx + t, a.W));
+            for (int t = 0; t < 2 * QL; ++t) ptx::cp_async_4(d + t, rowp + ix[t]);
           }
         }
         ptx::cp_async_arrive(bar);
         return;
       }
-      // synchronous fill: fp16 off the TMA path, or an axis of length 1
-      for (int j = 0; j < 2 * C::CH; ++j) {
+      // synchronous fill: float16 off the TMA path, or an axis of length 1
+      for (int j = 0; j < C::ROWS; ++j) {
         const int gy = sy0 + j;
         const bool rabs = (a.H == 1 && gy != 0);
         const ST* rowp = src + (long long)(a.H == 1 ? 0 : mirror(gy, a.H)) * pitch;
-        ST* d = dst + j * C::ROWE + off + 4 * lane;
+        ST* d = plane(s, 0) + j * C::ROWE + col;
 #pragma unroll
-        for (int t = 0; t < 4; ++t) {
-          const int gx = xs + 4 * lane + t;
-          const bool cabs = (a.W == 1 && gx != 0);
-          d[t] = (rabs || cabs) ? StoreT<ST>::from_v(VT(0))
-                                : rowp[a.W == 1 ? 0 : mirror(gx, a.W)];
+        for (int t = 0; t < 2 * QL; ++t) {
+          const int x = gx + t;
+          const bool cabs = (a.W == 1 && x != 0);
+          d[t] = (rabs || cabs) ? StoreT<ST>::from_v(VT(0)) : rowp[a.W == 1 ? 0 : mirror(x, a.W)];
         }
       }
       ptx::mbar_arrive(bar);
     } else {
-      // four subband planes; the lane covers quads mfirst + 2*lane + {0, 1}
-      const int xal = align_down(mfirst, C::A), off = mfirst - xal;
-      const bool inside = !tiny && y0 >= 0 && y0 + C::CH <= a.fh && mfirst >= 0 && mfirst + 64 <= a.fw;
+      // four subband planes; the lane covers quads mfirst + QL*lane + (0..QL-1)
+      const bool inside = !tiny && y0 >= 0 && y0 + C::CH <= a.fh && mfirst >= 0 && mfirst + C::WQ <= a.fw;
       if (inside && a.src_tma) {
         if (lane == 0) {
           ptx::fence_proxy_async_smem();
           ptx::mbar_arrive_expect_tx(bar, 4 * C::BOX_BYTES);
 #pragma unroll
           for (int p = 0; p < 4; ++p)
-            ptx::tma_load_2d(reinterpret_cast<unsigned char*>(dst) + p * C::PLANE_BYTES, &maps.m[p],
-                             xal, y0, bar);
+            ptx::tma_load_2d(plane(s, p), &maps.m[p], align_down(mfirst, C::A), y0, bar);
         } else {
           ptx::mbar_arrive(bar);
         }
         return;
       }
       const bool async = !tiny && C::ES == 4;
-      const int m = mfirst + 2 * lane;
+      const int m = mfirst + QL * lane;
 #pragma unroll
       for (int p = 0; p < 4; ++p) {
         const int py = p >> 1, px = p & 1;
         const int pw = px ? a.fw : a.cw, ph = py ? a.fh : a.ch;
-        ST* pd = reinterpret_cast<ST*>(reinterpret_cast<unsigned char*>(dst) + p * C::PLANE_BYTES);
         if (async) {
           // mirroring keeps the parity of a sample index, so a mirrored
           // element of plane p is again in plane p
-          int ix[2];
+          int ix[QL];
 #pragma unroll
-          for (int t = 0; t < 2; ++t) {
+          for (int t = 0; t < QL; ++t) {
             const int mm = m + t;
             ix[t] = (mm >= 0 && mm < pw) ? mm : (mirror(2 * mm + px, a.W) >> 1);
           }
-          const bool direct = m >= 0 && m + 2 <= pw;
+          const bool direct = m >= 0 && m + QL <= pw;
           for (int r = 0; r < C::CH; ++r) {
             const int y = y0 + r;
             const int iy = (y >= 0 && y < ph) ? y : (mirror(2 * y + py, a.H) >> 1);
             const ST* rowp = src_plane(p) + (long long)iy * a.src_pitch[p];
-            ST* d = pd + r * C::ROWE + off + 2 * lane;
-            if (direct && (reinterpret_cast<uintptr_t>(rowp + m) & 7) == 0) {
-              ptx::cp_async_8(d, rowp + m);
+            ST* d = plane(s, p) + r * C::ROWE + col;
+            if (direct && (reinterpret_cast<uintptr_t>(rowp + m) & (QL * 4 - 1)) == 0) {
+              if constexpr (QL == 4) ptx::cp_async_16(d, rowp + m);
+              else ptx::cp_async_8(d, rowp + m);
             } else {
-              ptx::cp_async_4(d, rowp + ix[0]);
-              ptx::cp_async_4(d + 1, rowp + ix[1]);
+#pragma unroll
+              for (int t = 0; t < QL; ++t) ptx::cp_async_4(d + t, rowp + ix[t]);
             }
           }
           continue;
         }
         for (int r = 0; r < C::CH; ++r) {
           const int y = y0 + r;
-          ST* d = pd + r * C::ROWE + off + 2 * lane;
+          ST* d = plane(s, p) + r * C::ROWE + col;
 #pragma unroll
-          for (int t = 0; t < 2; ++t) {
+          for (int t = 0; t < QL; ++t) {
             // sample coordinates of this element, mirrored, mapped back to a plane
             const int sy = 2 * y + py, sx = 2 * (m + t) + px;
             bool absent = false;
@@ -230,44 +273,29 @@ struct Strip {
   }
 
   // ---- consumer --------------------------------------------------------------
-  __device__ __forceinline__ Row<VT> load_row(const ST* st, int r) const {
-    Row<VT> o;
+  __device__ __forceinline__ Row<VT, QL> load_row(int s, int r) const {
+    Row<VT, QL> o;
+    const int col = lane_col();
     if constexpr (C::LOAD == SAMPLES) {
-      const int xs = 2 * mfirst;
-      const int off = xs - align_down(xs, C::A);
-      const ST* p0 = st + (2 * r) * C::ROWE + off + 4 * lane;
-      const ST* p1 = p0 + C::ROWE;
-      ST v0[4], v1[4];
-      if constexpr (C::ES == 4) {
-        *reinterpret_cast<int4*>(v0) = *reinterpret_cast<const int4*>(p0);
-        *reinterpret_cast<int4*>(v1) = *reinterpret_cast<const int4*>(p1);
-      } else {
-        *reinterpret_cast<int2*>(v0) = *reinterpret_cast<const int2*>(p0);
-        *reinterpret_cast<int2*>(v1) = *reinterpret_cast<const int2*>(p1);
+      // row 2r: LL HL LL HL ..., row 2r+1: LH HH LH HH ...
+      ST v0[2 * QL], v1[2 * QL];
+      const ST* p0 = plane(s, 0) + (2 * r) * C::ROWE + col;
+      copy_bytes<2 * QL * C::ES>(v0, p0);
+      copy_bytes<2 * QL * C::ES>(v1, p0 + C::ROWE);
+#pragma unroll
+      for (int j = 0; j < QL; ++j) {
+        o.s[LL][j] = StoreT<ST>::to_v(v0[2 * j]);
+        o.s[HL][j] = StoreT<ST>::to_v(v0[2 * j + 1]);
+        o.s[LH][j] = StoreT<ST>::to_v(v1[2 * j]);
+        o.s[HH][j] = StoreT<ST>::to_v(v1[2 * j + 1]);
       }
-      o.s[LL][0] = StoreT<ST>::to_v(v0[0]);
-      o.s[HL][0] = StoreT<ST>::to_v(v0[1]);
-      o.s[LL][1] = StoreT<ST>::to_v(v0[2]);
-      o.s[HL][1] = StoreT<ST>::to_v(v0[3]);
-      o.s[LH][0] = StoreT<ST>::to_v(v1[0]);
-      o.s[HH][0] = StoreT<ST>::to_v(v1[1]);
-      o.s[LH][1] = StoreT<ST>::to_v(v1[2]);
-      o.s[HH][1] = StoreT<ST>::to_v(v1[3]);
     } else {
-      const int off = mfirst - align_down(mfirst, C::A);
 #pragma unroll
       for (int p = 0; p < 4; ++p) {
-        const ST* pp = reinterpret_cast<const ST*>(reinterpret_cast<const unsigned char*>(st) +
-                                                   p * C::PLANE_BYTES) +
-                       r * C::ROWE + off + 2 * lane;
-        ST v[2];
-        if constexpr (C::ES == 4) {
-          *reinterpret_cast<int2*>(v) = *reinterpret_cast<const int2*>(pp);
-        } else {
-          *reinterpret_cast<int*>(v) = *reinterpret_cast<const int*>(pp);
-        }
-        o.s[p][0] = StoreT<ST>::to_v(v[0]);
-        o.s[p][1] = StoreT<ST>::to_v(v[1]);
+        ST v[QL];
+        copy_bytes<QL * C::ES>(v, plane(s, p) + r * C::ROWE + col);
+#pragma unroll
+        for (int j = 0; j < QL; ++j) o.s[p][j] = StoreT<ST>::to_v(v[j]);
       }
     }
     return o;
@@ -278,83 +306,76 @@ struct Strip {
     ST* base[4];
     long long pitch[4];
     int rows[4];
-    bool pair[4];   // both quads stored with one vector access
-    bool one[2];    // quad a / quad b stored (SUBBANDS) or sample columns (SAMPLES)
+    bool vec[4];  // the lane's elements of this plane are stored as one vector
     bool lane_ok;
   };
 
   __device__ __forceinline__ Out out_bases() const {
     Out o;
-    const int m = mfirst + 2 * lane;
+    const int m = mfirst + QL * lane;
     o.lane_ok = m >= m0 && m < m0 + C::UQ;
     if constexpr (C::STORE == SUBBANDS) {
+      constexpr int VB = QL * C::ES;  // bytes of the lane's row segment
 #pragma unroll
       for (int p = 0; p < 4; ++p) {
         const int pw = (p & 1) ? a.fw : a.cw;
         o.rows[p] = (p >> 1) ? a.fh : a.ch;
         o.base[p] = static_cast<ST*>(a.dst[p]) + m;
         o.pitch[p] = a.dst_pitch[p];
-        o.pair[p] = m + 2 <= pw && ((reinterpret_cast<uintptr_t>(o.base[p]) & (2 * C::ES - 1)) == 0) &&
-                    ((a.dst_pitch[p] * C::ES) & (2 * C::ES - 1)) == 0;
-        if (p == 0) {
-          o.one[0] = m < pw;
-          o.one[1] = m + 1 < pw;
-        }
+        o.vec[p] = m + QL <= pw && ((reinterpret_cast<uintptr_t>(o.base[p]) & (VB - 1)) == 0) &&
+                   ((a.dst_pitch[p] * C::ES) & (VB - 1)) == 0;
       }
     } else {
+      constexpr int VB = 2 * QL * C::ES;
       const int gx = 2 * m;
       o.base[0] = static_cast<ST*>(a.dst[0]) + gx;
       o.pitch[0] = a.dst_pitch[0];
       o.rows[0] = a.H;
-      o.pair[0] = gx + 4 <= a.W && ((reinterpret_cast<uintptr_t>(o.base[0]) & (4 * C::ES - 1)) == 0) &&
-                  ((a.dst_pitch[0] * C::ES) & (4 * C::ES - 1)) == 0;
+      o.vec[0] = gx + 2 * QL <= a.W && ((reinterpret_cast<uintptr_t>(o.base[0]) & (VB - 1)) == 0) &&
+                 ((a.dst_pitch[0] * C::ES) & (VB - 1)) == 0;
     }
     return o;
   }
 
-  __device__ __forceinline__ void store_row(const Out& o, const Row<VT>& r, int q) const {
+  __device__ __forceinline__ void store_row(const Out& o, const Row<VT, QL>& r, int q) const {
     if (!o.lane_ok) return;  // halo lane
+    const int m = mfirst + QL * lane;
     if constexpr (C::STORE == SUBBANDS) {
-      const int m = mfirst + 2 * lane;
 #pragma unroll
       for (int p = 0; p < 4; ++p) {
         if (q >= o.rows[p]) continue;
         ST* rowp = o.base[p] + (long long)q * o.pitch[p];
-        const ST v0 = StoreT<ST>::from_v(r.s[p][0]), v1 = StoreT<ST>::from_v(r.s[p][1]);
-        if (o.pair[p]) {
-          if constexpr (C::ES == 4) {
-            int2 pk;
-            pk.x = *reinterpret_cast<const int*>(&v0);
-            pk.y = *reinterpret_cast<const int*>(&v1);
-            *reinterpret_cast<int2*>(rowp) = pk;
-          } else {
-            __half2 h;
-            h.x = *reinterpret_cast<const __half*>(&v0);
-            h.y = *reinterpret_cast<const __half*>(&v1);
-            *reinterpret_cast<__half2*>(rowp) = h;
-          }
+        ST v[QL];
+#pragma unroll
+        for (int j = 0; j < QL; ++j) v[j] = StoreT<ST>::from_v(r.s[p][j]);
+        if (o.vec[p]) {
+          copy_bytes<QL * C::ES>(rowp, v);
         } else {
           const int pw = (p & 1) ? a.fw : a.cw;
-          if (m < pw) rowp[0] = v0;
-          if (m + 1 < pw) rowp[1] = v1;
+#pragma unroll
+          for (int j = 0; j < QL; ++j)
+            if (m + j < pw) rowp[j] = v[j];
         }
       }
     } else {
-      const int gx = 2 * (mfirst + 2 * lane);
+      const int gx = 2 * m;
 #pragma unroll
       for (int rr = 0; rr < 2; ++rr) {
         const int gy = 2 * q + rr;
         if (gy >= o.rows[0]) continue;
         ST* rowp = o.base[0] + (long long)gy * o.pitch[0];
         const int sl = rr ? LH : LL, sh = rr ? HH : HL;
-        ST v[4] = {StoreT<ST>::from_v(r.s[sl][0]), StoreT<ST>::from_v(r.s[sh][0]),
-                   StoreT<ST>::from_v(r.s[sl][1]), StoreT<ST>::from_v(r.s[sh][1])};
-        if (o.pair[0]) {
-          if constexpr (C::ES == 4) *reinterpret_cast<int4*>(rowp) = *reinterpret_cast<const int4*>(v);
-          else *reinterpret_cast<int2*>(rowp) = *reinterpret_cast<const int2*>(v);
+        ST v[2 * QL];
+#pragma unroll
+        for (int j = 0; j < QL; ++j) {
+          v[2 * j] = StoreT<ST>::from_v(r.s[sl][j]);
+          v[2 * j + 1] = StoreT<ST>::from_v(r.s[sh][j]);
+        }
+        if (o.vec[0]) {
+          copy_bytes<2 * QL * C::ES>(rowp, v);
         } else {
 #pragma unroll
-          for (int t = 0; t < 4; ++t)
+          for (int t = 0; t < 2 * QL; ++t)
             if (gx + t < a.W) rowp[t] = v[t];
         }
       }
@@ -363,14 +384,15 @@ struct Strip {
 };
 
 template <class C>
-__global__ void __launch_bounds__(kWarpsPerCta * 32)
+__global__ void __launch_bounds__(kWarpsPerCta * 32, C::MIN_BLOCKS)
     level_kernel(const __grid_constant__ TmaMaps maps, const __grid_constant__ LevelArgs a,
                  const __grid_constant__ Coefs cf, const __grid_constant__ ConvTaps ct) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int cs = blockIdx.x * kWarpsPerCta + warp;
-  if (cs >= a.ncs) return;  // whole warp: no CTA-wide synchronisation is used
-  const int q0 = blockIdx.y * a.T;
+  const int strip = blockIdx.x * kWarpsPerCta + warp;
+  if (strip >= a.ncs * a.nrs) return;  // whole warp: no CTA-wide synchronisation is used
+  const int cs = strip % a.ncs, rs = strip / a.ncs;
+  const int q0 = rs * a.T;
   const int rows_out = min(a.T, a.ch - q0);
   if (rows_out <= 0) return;
   const int NS = a.nstages;
@@ -394,7 +416,7 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32)
   for (int c = 0; c < NS - 1 && c < nchunks; ++c) sp.fill(c, c);
 
   const typename Strip<C>::Out ob = sp.out_bases();
-  Pipe<typename C::VT, typename C::PROG> pipe;
+  Pipe<typename C::VT, C::QL, typename C::PROG> pipe;
   pipe.reset();
   for (int c = 0; c < nchunks; ++c) {
     const int cn = c + NS - 1;
@@ -413,14 +435,13 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32)
         ptx::mbar_wait_bounded(&sp.bars[k % NS], (k / NS) & 1, kWaitProbes);
       return;
     }
-    const typename C::ST* st = sp.stage(s);
     const int qc = sp.yfirst + c * C::CH - Tot::DOWN;
-    // unrolled by two rows: the stage windows rotate with period two, and
-    // the loop body stays small enough for the instruction cache
+    // two rows per unrolled body: the stage windows rotate with period two,
+    // and the loop body stays small enough for the instruction cache
 #pragma unroll 2
     for (int r = 0; r < C::CH; ++r) {
-      const Row<typename C::VT> in = sp.load_row(st, r);
-      const Row<typename C::VT> out = pipe.push(in, cf, ct);
+      const Row<typename C::VT, C::QL> in = sp.load_row(s, r);
+      const Row<typename C::VT, C::QL> out = pipe.push(in, cf, ct);
       const int q = qc + r;
       if (q >= q0 && q < q_end) sp.store_row(ob, out, q);
     }
@@ -442,7 +463,7 @@ struct Instance {
     k.load = (Layout)C::LOAD;
     k.store = (Layout)C::STORE;
     k.box_w = C::ROWE;
-    k.box_h = C::LOAD == SAMPLES ? 2 * C::CH : C::CH;
+    k.box_h = C::ROWS;
     k.smem_bytes = smem(nstages);
     k.fn = reinterpret_cast<const void*>(&level_kernel<C>);
     k.supported = true;
@@ -462,7 +483,8 @@ struct Instance {
       if (e != cudaSuccess) return e;
       configured[dev] = 1;
     }
-    dim3 grid((a.ncs + kWarpsPerCta - 1) / kWarpsPerCta, a.nrs);
+    const long long strips = (long long)a.ncs * a.nrs;
+    dim3 grid((unsigned)((strips + kWarpsPerCta - 1) / kWarpsPerCta));
     level_kernel<C><<<grid, kWarpsPerCta * 32, bytes, s>>>(m, a, cf, ct);
     return cudaGetLastError();
   }

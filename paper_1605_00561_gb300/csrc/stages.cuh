@@ -2,10 +2,10 @@
 //
 // A quadruple (n, m) holds the samples of rows 2n..2n+1 and columns
 // 2m..2m+1: LL (even, even), HL (even, odd), LH (odd, even), HH (odd, odd)
-// (Sec. 2.3).  A lane of a warp holds two horizontally adjacent
-// quadruples ("a" = 2l, "b" = 2l+1 relative to the warp's first quad), so a
-// horizontal neighbour at distance <= 2 is either in the lane or one shuffle
-// away.  Vertical neighbours come from the stage's window of rows.
+// (Sec. 2.3).  A lane of a warp holds QL horizontally adjacent quadruples
+// (QL*l .. QL*l + QL-1 relative to the warp's first quad), so a horizontal
+// neighbour at distance <= QL is either in the lane or one shuffle away.
+// Vertical neighbours come from the stage's window of rows.
 //
 // A linear stage is one step matrix of the paper: every target subband
 // receives sum(sign * (vertical op (x) horizontal op) applied to a source
@@ -51,22 +51,20 @@ __host__ __device__ constexpr int vmin(int a, A... b) {
 
 enum Sub : int { LL = 0, HL = 1, LH = 2, HH = 3 };
 
-template <typename V>
+template <typename V, int QL>
 struct Row {
-  V s[4][2];
+  V s[4][QL];
 };
 
-// The value of the quad at position P, where 0 and 1 are this lane's quads
-// a and b, -2/-1 the previous lane's and 2/3 the next lane's.
-template <int P, typename V>
-__device__ __forceinline__ V hpos(const V (&x)[2]) {
-  static_assert(P >= -2 && P <= 3, "horizontal reach beyond the neighbouring lane");
-  if constexpr (P == 0) return x[0];
-  else if constexpr (P == 1) return x[1];
-  else if constexpr (P == -1) return __shfl_up_sync(kFull, x[1], 1);
-  else if constexpr (P == -2) return __shfl_up_sync(kFull, x[0], 1);
-  else if constexpr (P == 2) return __shfl_down_sync(kFull, x[0], 1);
-  else return __shfl_down_sync(kFull, x[1], 1);
+// The value of the quad at position P, where 0..QL-1 are this lane's quads,
+// negative positions the previous lane's last ones and QL.. the next lane's
+// first ones.
+template <int P, typename V, int QL>
+__device__ __forceinline__ V hpos(const V (&x)[QL]) {
+  static_assert(P >= -QL && P < 2 * QL, "horizontal reach beyond the neighbouring lane");
+  if constexpr (P >= 0 && P < QL) return x[P];
+  else if constexpr (P < 0) return __shfl_up_sync(kFull, x[QL + P], 1);
+  else return __shfl_down_sync(kFull, x[P - QL], 1);
 }
 
 // ---------------------------------------------------------------------------
@@ -164,8 +162,9 @@ struct Lin {
   // roundings at the magnitude of the target than one FMA per tap.  The
   // class holding the centre tap, whose coefficient is the largest in the
   // products of V, is accumulated in the second pass, after all others.
-  template <class T, bool CENTRE_PASS>
-  __device__ __forceinline__ static void term(const Row<float>* w, Row<float>& o, const Coefs& c) {
+  template <class T, bool CENTRE_PASS, int QL>
+  __device__ __forceinline__ static void term(const Row<float, QL>* w, Row<float, QL>& o,
+                                              const Coefs& c) {
     using VS = OpShape<DEG, T::vop>;
     using HS = OpShape<DEG, T::hop>;
     static_for<0, VS::NCLS - 1>([&](auto cvi) {
@@ -175,60 +174,60 @@ struct Lin {
         constexpr bool centre = VS::has(0) && HS::has(0) && VS::cls(0) == CV && HS::cls(0) == CH &&
                                 VS::lo <= 0 && VS::hi >= 0 && HS::lo <= 0 && HS::hi >= 0;
         if constexpr (centre == CENTRE_PASS) {
-          float s0 = 0.0f, s1 = 0.0f;
+          float s[QL];
           bool first = true;
           static_for<VS::lo, VS::hi>([&](auto dy) {
             constexpr int DY = decltype(dy)::value;
             if constexpr (VS::has(DY) && VS::cls(DY) == CV) {
-              const float(&x)[2] = w[UP + DY].s[T::src];
+              const float(&x)[QL] = w[UP + DY].s[T::src];
               static_for<HS::lo, HS::hi>([&](auto dx) {
                 constexpr int DX = decltype(dx)::value;
                 if constexpr (HS::has(DX) && HS::cls(DX) == CH) {
-                  const float a0 = hpos<0 + DX>(x), a1 = hpos<1 + DX>(x);
-                  if (first) {
-                    s0 = a0;
-                    s1 = a1;
-                    first = false;
-                  } else {
-                    s0 += a0;
-                    s1 += a1;
-                  }
+                  static_for<0, QL - 1>([&](auto jj) {
+                    constexpr int J = decltype(jj)::value;
+                    const float v = hpos<J + DX>(x);
+                    s[J] = first ? v : s[J] + v;
+                  });
+                  first = false;
                 }
               });
             }
           });
           const float cf = (T::sgn > 0 ? 1.0f : -1.0f) * op_tap<DEG, T::vop, K, 0, VS::rep(CV)>(c) *
                            op_tap<DEG, T::hop, K, 1, HS::rep(CH)>(c);
-          o.s[T::tgt][0] = fmaf(cf, s0, o.s[T::tgt][0]);
-          o.s[T::tgt][1] = fmaf(cf, s1, o.s[T::tgt][1]);
+#pragma unroll
+          for (int j = 0; j < QL; ++j) o.s[T::tgt][j] = fmaf(cf, s[j], o.s[T::tgt][j]);
         }
       });
     });
   }
 
-  __device__ __forceinline__ static void eval(const Row<float>* w, Row<float>& o, const Coefs& c,
-                                              const ConvTaps&) {
+  template <int QL>
+  __device__ __forceinline__ static void eval(const Row<float, QL>* w, Row<float, QL>& o,
+                                              const Coefs& c, const ConvTaps&) {
     o = w[UP];
     if constexpr (REPLACE) {
 #pragma unroll
       for (int s = 0; s < 4; ++s)
-        if (TARGETS & (1u << s)) o.s[s][0] = o.s[s][1] = 0.0f;
+        if (TARGETS & (1u << s))
+#pragma unroll
+          for (int j = 0; j < QL; ++j) o.s[s][j] = 0.0f;
     }
-    (term<Ts, false>(w, o, c), ...);
-    (term<Ts, true>(w, o, c), ...);
+    (term<Ts, false, QL>(w, o, c), ...);
+    (term<Ts, true, QL>(w, o, c), ...);
   }
 };
 
 // Scaling step (Sec. 2.2, the diagonal matrix of M): per-subband factors.
 struct Scale {
   static constexpr int UP = 0, DOWN = 0, LEFT = 0, RIGHT = 0;
-  __device__ __forceinline__ static void eval(const Row<float>* w, Row<float>& o, const Coefs& c,
-                                              const ConvTaps&) {
+  template <int QL>
+  __device__ __forceinline__ static void eval(const Row<float, QL>* w, Row<float, QL>& o,
+                                              const Coefs& c, const ConvTaps&) {
 #pragma unroll
-    for (int s = 0; s < 4; ++s) {
-      o.s[s][0] = w[0].s[s][0] * c.scale[s];
-      o.s[s][1] = w[0].s[s][1] * c.scale[s];
-    }
+    for (int s = 0; s < 4; ++s)
+#pragma unroll
+      for (int j = 0; j < QL; ++j) o.s[s][j] = w[0].s[s][j] * c.scale[s];
   }
 };
 
@@ -260,26 +259,31 @@ struct Conv {
   static constexpr int DOWN = cmax(cmax(S::hi(0, 0), S::hi(0, 1)), cmax(S::hi(1, 0), S::hi(1, 1)));
   static constexpr int LEFT = UP, RIGHT = DOWN;
 
-  __device__ __forceinline__ static void eval(const Row<float>* w, Row<float>& o, const Coefs&,
-                                              const ConvTaps& t) {
+  template <int QL>
+  __device__ __forceinline__ static void eval(const Row<float, QL>* w, Row<float, QL>& o,
+                                              const Coefs&, const ConvTaps& t) {
     static_for<0, 3>([&](auto so_sx) {
       constexpr int SO = decltype(so_sx)::value >> 1, SX = decltype(so_sx)::value & 1;
-      float acc0 = 0.0f, acc1 = 0.0f;
+      float acc[QL];
+#pragma unroll
+      for (int j = 0; j < QL; ++j) acc[j] = 0.0f;
       static_for<0, 3>([&](auto ti_tx) {
         constexpr int TI = decltype(ti_tx)::value >> 1, TX = decltype(ti_tx)::value & 1;
         static_for<S::lo(SO, TI), S::hi(SO, TI)>([&](auto dy) {
           constexpr int DY = decltype(dy)::value;
-          const float(&x)[2] = w[UP + DY].s[2 * TI + TX];
+          const float(&x)[QL] = w[UP + DY].s[2 * TI + TX];
           static_for<S::lo(SX, TX), S::hi(SX, TX)>([&](auto dx) {
             constexpr int DX = decltype(dx)::value;
             const float cf = t.t[SO][SX][TI][TX][DY + 2][DX + 2];
-            acc0 = fmaf(cf, hpos<0 + DX>(x), acc0);
-            acc1 = fmaf(cf, hpos<1 + DX>(x), acc1);
+            static_for<0, QL - 1>([&](auto jj) {
+              constexpr int J = decltype(jj)::value;
+              acc[J] = fmaf(cf, hpos<J + DX>(x), acc[J]);
+            });
           });
         });
       });
-      o.s[2 * SO + SX][0] = acc0;
-      o.s[2 * SO + SX][1] = acc1;
+#pragma unroll
+      for (int j = 0; j < QL; ++j) o.s[2 * SO + SX][j] = acc[j];
     });
   }
 };
@@ -297,14 +301,15 @@ struct Int53 {
   static constexpr int LEFT = KIND == 3 ? 1 : 0;
   static constexpr int RIGHT = KIND == 2 ? 1 : 0;
 
-  __device__ __forceinline__ static void eval(const Row<int>* w, Row<int>& o, const Coefs& c,
-                                              const ConvTaps&) {
+  template <int QL>
+  __device__ __forceinline__ static void eval(const Row<int, QL>* w, Row<int, QL>& o,
+                                              const Coefs& c, const ConvTaps&) {
     o = w[UP];
     const int sg = INV ? -1 : 1;
     if constexpr (KIND == 0) {  // odd rows -= floor((even above + even below) / 2)
       if (c.v_on) {
 #pragma unroll
-        for (int j = 0; j < 2; ++j) {
+        for (int j = 0; j < QL; ++j) {
           o.s[LH][j] -= sg * ((w[0].s[LL][j] + w[1].s[LL][j]) >> 1);
           o.s[HH][j] -= sg * ((w[0].s[HL][j] + w[1].s[HL][j]) >> 1);
         }
@@ -312,30 +317,32 @@ struct Int53 {
     } else if constexpr (KIND == 1) {  // even rows += floor((odd above + odd below + 2) / 4)
       if (c.v_on) {
 #pragma unroll
-        for (int j = 0; j < 2; ++j) {
+        for (int j = 0; j < QL; ++j) {
           o.s[LL][j] += sg * ((w[0].s[LH][j] + w[1].s[LH][j] + 2) >> 2);
           o.s[HL][j] += sg * ((w[0].s[HH][j] + w[1].s[HH][j] + 2) >> 2);
         }
       }
-    } else if constexpr (KIND == 2) {
+    } else if constexpr (KIND == 2) {  // odd columns from the even ones at m, m+1
       if (c.h_on) {
-        const int* ll = w[0].s[LL];
-        const int* lh = w[0].s[LH];
-        const int llr = hpos<2>(w[0].s[LL]), lhr = hpos<2>(w[0].s[LH]);
-        o.s[HL][0] -= sg * ((ll[0] + ll[1]) >> 1);
-        o.s[HL][1] -= sg * ((ll[1] + llr) >> 1);
-        o.s[HH][0] -= sg * ((lh[0] + lh[1]) >> 1);
-        o.s[HH][1] -= sg * ((lh[1] + lhr) >> 1);
+        const int llr = hpos<QL>(w[0].s[LL]), lhr = hpos<QL>(w[0].s[LH]);
+#pragma unroll
+        for (int j = 0; j < QL; ++j) {
+          const int lln = j + 1 < QL ? w[0].s[LL][j + 1] : llr;
+          const int lhn = j + 1 < QL ? w[0].s[LH][j + 1] : lhr;
+          o.s[HL][j] -= sg * ((w[0].s[LL][j] + lln) >> 1);
+          o.s[HH][j] -= sg * ((w[0].s[LH][j] + lhn) >> 1);
+        }
       }
-    } else {
+    } else {  // even columns from the odd ones at m-1, m
       if (c.h_on) {
-        const int* hl = w[0].s[HL];
-        const int* hh = w[0].s[HH];
         const int hll = hpos<-1>(w[0].s[HL]), hhl = hpos<-1>(w[0].s[HH]);
-        o.s[LL][0] += sg * ((hll + hl[0] + 2) >> 2);
-        o.s[LL][1] += sg * ((hl[0] + hl[1] + 2) >> 2);
-        o.s[LH][0] += sg * ((hhl + hh[0] + 2) >> 2);
-        o.s[LH][1] += sg * ((hh[0] + hh[1] + 2) >> 2);
+#pragma unroll
+        for (int j = 0; j < QL; ++j) {
+          const int hlp = j > 0 ? w[0].s[HL][j - 1] : hll;
+          const int hhp = j > 0 ? w[0].s[HH][j - 1] : hhl;
+          o.s[LL][j] += sg * ((hlp + w[0].s[HL][j] + 2) >> 2);
+          o.s[LH][j] += sg * ((hhp + w[0].s[HH][j] + 2) >> 2);
+        }
       }
     }
   }
@@ -367,37 +374,40 @@ struct Totals<List<S...>> {
 // A chain of stages; each keeps the rows of its input state it still needs.
 // push() takes the next input row and returns the last stage's output for
 // the row sum(DOWN) positions behind it.
-template <typename V, class L>
+template <typename V, int QL, class L>
 struct Pipe;
 
-template <typename V>
-struct Pipe<V, List<>> {
+template <typename V, int QL>
+struct Pipe<V, QL, List<>> {
   __device__ __forceinline__ void reset() {}
-  __device__ __forceinline__ Row<V> push(const Row<V>& r, const Coefs&, const ConvTaps&) {
+  __device__ __forceinline__ Row<V, QL> push(const Row<V, QL>& r, const Coefs&, const ConvTaps&) {
     return r;
   }
 };
 
-template <typename V, class S0, class... S>
-struct Pipe<V, List<S0, S...>> {
+template <typename V, int QL, class S0, class... S>
+struct Pipe<V, QL, List<S0, S...>> {
   static constexpr int NW = S0::UP + 1 + S0::DOWN;
-  Row<V> win[NW];
-  Pipe<V, List<S...>> rest;
+  Row<V, QL> win[NW];
+  Pipe<V, QL, List<S...>> rest;
 
   __device__ __forceinline__ void reset() {
 #pragma unroll
     for (int k = 0; k < NW; ++k)
 #pragma unroll
-      for (int s = 0; s < 4; ++s) win[k].s[s][0] = win[k].s[s][1] = V(0);
+      for (int s = 0; s < 4; ++s)
+#pragma unroll
+        for (int j = 0; j < QL; ++j) win[k].s[s][j] = V(0);
     rest.reset();
   }
 
-  __device__ __forceinline__ Row<V> push(const Row<V>& r, const Coefs& c, const ConvTaps& t) {
+  __device__ __forceinline__ Row<V, QL> push(const Row<V, QL>& r, const Coefs& c,
+                                             const ConvTaps& t) {
 #pragma unroll
     for (int k = 0; k + 1 < NW; ++k) win[k] = win[k + 1];
     win[NW - 1] = r;
-    Row<V> o;
-    S0::eval(win, o, c, t);
+    Row<V, QL> o;
+    S0::template eval<QL>(win, o, c, t);
     return rest.push(o, c, t);
   }
 };
