@@ -102,7 +102,7 @@ dwt_status dwt_plan_create(int w, int h, dwt_wavelet wavelet, int levels, dwt_dt
 dwt_status dwt_plan_set_scheme(dwt_plan plan, dwt_scheme scheme);
 
 /* Tile shape of the kernels (autotuner knobs).  min_strip_rows: the least
- * number of quadruple rows a warp streams (0 = default 8); a launch uses
+ * number of quadruple rows a warp streams (0 = default 2); a launch uses
  * longer strips when that still fills every SM once.  stages: depth of each
  * warp's shared-memory ring of row chunks, 1..4 (0 = default); deeper rings
  * keep more loads in flight per warp, shallower ones let more warps reside.

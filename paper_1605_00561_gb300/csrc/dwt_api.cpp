@@ -330,7 +330,7 @@ struct dwt_plan_s {
   std::vector<ProfRec> pending;
   std::vector<cudaEvent_t> pool;
   int nstages = kDefaultStages;
-  int tmin = 8;
+  int tmin = 2;
   std::mutex mu;
 };
 
@@ -750,7 +750,7 @@ dwt_status dwt_plan_set_tile(dwt_plan p, int min_strip_rows, int stages) {
   if (!p || min_strip_rows < 0 || min_strip_rows > 1 << 20 || stages < 0 || stages > kMaxStages)
     return DWT_EINVAL;
   std::lock_guard<std::mutex> lk(p->mu);
-  p->tmin = min_strip_rows ? min_strip_rows : 8;
+  p->tmin = min_strip_rows ? min_strip_rows : 2;
   p->nstages = stages ? stages : kDefaultStages;
   return DWT_OK;
 }
