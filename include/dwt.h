@@ -127,6 +127,29 @@ dwt_status dwt2_forward(dwt_plan plan, const void* d_in, size_t in_pitch_bytes, 
 dwt_status dwt2_inverse(dwt_plan plan, const void* d_coef, size_t coef_pitch_bytes, void* d_out,
                         size_t out_pitch_bytes, dwt_stream stream);
 
+/* Forward transform for callers that cannot allocate device memory: code
+ * that runs while a CUDA graph is being captured, real-time loops that must
+ * not call cudaMalloc (it can synchronise the device and take unbounded
+ * time), and host frameworks that own every allocation themselves.  The
+ * paper has no counterpart; it is the plan-free twin of dwt2_forward with
+ * the default scheme (Monolithic* for float, the separable JPEG 2000 order
+ * for int32) and default tile.  The caller passes the input and output as
+ * for dwt2_forward; the LL scratch of the pyramid and a device status word
+ * live in one file-scope device array of this library, 32 MiB plus 256
+ * bytes, which every GPU that loads the library holds until the process
+ * exits.  Images whose LL scratch (row pitch ceil(w/2) elements rounded up
+ * to 128 bytes, times ceil(h/2) + ceil(h/4) rows; none for levels <= 1)
+ * exceeds 32 MiB -- above about 4096 x 4096 float32 -- are rejected with
+ * DWT_EINVAL.  The call makes no cudaMalloc, cudaFree or other allocating
+ * call.  The first call on each device looks up the array's device address
+ * (once per device, with that device current); make that first call before
+ * any stream capture.  All calls share the array and it keeps the previous
+ * call's contents: calls that overlap on the GPU (other streams, or another
+ * thread) race on it, so serialise them. */
+dwt_status dwt2_forward_noalloc(int w, int h, dwt_wavelet wavelet, int levels, dwt_dtype dtype,
+                                const void* d_in, size_t in_pitch_bytes, void* d_out,
+                                size_t out_pitch_bytes, dwt_stream stream);
+
 /* Same transforms with HOST buffers: the call copies the input to device
  * staging owned by the plan, transforms it, and copies the result back into
  * h_out, all on `stream`.  h_in / h_out should be page-locked for the

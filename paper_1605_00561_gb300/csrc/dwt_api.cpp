@@ -668,6 +668,103 @@ struct DeviceGuard {
 }  // namespace
 
 // ---------------------------------------------------------------------------
+// Forward transform on caller-provided scratch, for the entry point that
+// allocates nothing (noalloc.cu).  It mirrors the plan path's forward level
+// loop with the default scheme and tile, keeps its state on the stack, and
+// makes no device or host allocation.
+// ---------------------------------------------------------------------------
+namespace dwt {
+
+dwt_status forward_on_scratch(int w, int h, int wavelet, int levels, int dtype, const void* src,
+                              size_t src_pitch, void* dst, size_t dst_pitch, void* scratch,
+                              size_t scratch_bytes, int* d_status, cudaStream_t s) {
+  if (w < 1 || h < 1 || levels < 0 || levels > 30) return DWT_EINVAL;
+  if (wavelet < 0 || wavelet > 2 || dtype < 0 || dtype > 2) return DWT_EINVAL;
+  int Wk[32], Hk[32];
+  Wk[0] = w;
+  Hk[0] = h;
+  int maxl = 0;
+  for (int a = w, b = h; a > 1 || b > 1; a = (a + 1) / 2, b = (b + 1) / 2) ++maxl;
+  if (levels > maxl) return DWT_EINVAL;
+  for (int k = 1; k <= levels + 1 && k < 32; ++k) {
+    Wk[k] = (Wk[k - 1] + 1) / 2;
+    Hk[k] = (Hk[k - 1] + 1) / 2;
+  }
+  const int scheme = dtype == DWT_I32 ? DWT_SWELDENS : DWT_MONOLITHIC_S;
+  if (!scheme_supported(wavelet, dtype, scheme)) return DWT_EUNSUPPORTED;
+  const size_t es = elem_size(dtype);
+  if (src_pitch < (size_t)w * es || dst_pitch < (size_t)w * es || src_pitch % es || dst_pitch % es)
+    return DWT_EINVAL;
+  int device = -1;
+  if (cudaGetDevice(&device) != cudaSuccess) return DWT_ECUDA;
+  const size_t nsrc = plane_extent(w, h, src_pitch, es), ndst = plane_extent(w, h, dst_pitch, es);
+  if (!device_pointer_ok(src, nsrc, device) || !device_pointer_ok(dst, ndst, device)) return DWT_EINVAL;
+  if (overlaps(src, nsrc, dst, ndst)) return DWT_EINVAL;
+  // LL ping-pong: LL_0, LL_2, ... in the first region, LL_1, LL_3, ... in the second
+  const size_t spitch = levels >= 2 ? round_up((size_t)Wk[1] * es, 128) : 0;
+  const size_t need = levels >= 2 ? spitch * ((size_t)Hk[1] + Hk[2]) : 0;
+  if (need > scratch_bytes) return DWT_EINVAL;
+  if (levels == 0)
+    return from_cuda(cudaMemcpy2DAsync(dst, dst_pitch, src, src_pitch, (size_t)w * es, h,
+                                       cudaMemcpyDeviceToDevice, s));
+  char* sbase = static_cast<char*>(scratch);
+  void* sc[2] = {sbase, sbase + spitch * (size_t)Hk[1]};
+  const Lifting L = lifting_of(wavelet);
+  for (int k = 0; k < levels; ++k) {
+    LevelArgs a{};
+    a.W = Wk[k];
+    a.H = Hk[k];
+    a.cw = (a.W + 1) / 2;
+    a.ch = (a.H + 1) / 2;
+    a.fw = a.W / 2;
+    a.fh = a.H / 2;
+    char* ob = static_cast<char*>(dst);
+    a.src[0] = k == 0 ? src : sc[(k - 1) & 1];
+    a.src_pitch[0] = (long long)((k == 0 ? src_pitch : spitch) / es);
+    a.dst[0] = k == levels - 1 ? dst : sc[k & 1];
+    a.dst_pitch[0] = (long long)((k == levels - 1 ? dst_pitch : spitch) / es);
+    a.dst[1] = ob + a.cw * es;
+    a.dst[2] = ob + a.ch * dst_pitch;
+    a.dst[3] = ob + a.ch * dst_pitch + a.cw * es;
+    for (int i = 1; i < 4; ++i) a.dst_pitch[i] = (long long)(dst_pitch / es);
+    const Coefs cf = make_coefs(L, DWT_NORM_JPEG2000, a.W, a.H, PASS_FUSED, false);
+    ConvTaps ct;
+    std::memset(&ct, 0, sizeof ct);
+    const LaunchKey key{wavelet, dtype, scheme, PASS_FUSED, 0};
+    KernelInfo ki{};
+    if (!find_kernel(key, kDefaultStages, &ki)) return DWT_EUNSUPPORTED;
+    int sms = 0, per_sm = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+    int optin = 0;
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+    cudaFuncSetAttribute(ki.fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         optin > 0 ? optin : (int)ki.smem_bytes);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ki.fn, kWarpsPerCta * 32,
+                                                      ki.smem_bytes) != cudaSuccess)
+      per_sm = 1;
+    const int cap = std::max(sms, 1) * std::max(per_sm, 1);
+    a.ncs = (a.cw + ki.uq - 1) / ki.uq;
+    const int nrs_target = std::max(1, cap * kWarpsPerCta / a.ncs);
+    a.T = std::max(2, (a.ch + nrs_target - 1) / nrs_target);
+    a.nrs = (a.ch + a.T - 1) / a.T;
+    a.nstages = kDefaultStages;
+    a.status = d_status;
+    TmaMaps maps;
+    std::memset(&maps, 0, sizeof maps);
+    a.src_tma = 0;
+    if (a.W >= 2 && a.H >= 2)
+      a.src_tma = encode_2d(&maps.m[0], dtype, a.src[0], a.W, a.H, (size_t)a.src_pitch[0] * es,
+                            ki.box_w, ki.box_h);
+    const LaunchCall call{&a, &maps, &cf, &ct, s};
+    const cudaError_t e = call_kernel(key, kDefaultStages, call);
+    if (e != cudaSuccess) return from_cuda(e);
+  }
+  return DWT_OK;
+}
+
+}  // namespace dwt
+
+// ---------------------------------------------------------------------------
 // C ABI
 // ---------------------------------------------------------------------------
 extern "C" {

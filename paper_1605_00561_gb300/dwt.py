@@ -18,7 +18,7 @@ __all__ = [
     "DWT_CDF53", "DWT_CDF97", "DWT_DD137", "DWT_F32", "DWT_F16S", "DWT_I32",
     "SCHEMES", "DWT_NORM_JPEG2000", "DWT_NORM_ZETA",
     "dwt_plan_create", "dwt_plan_set_scheme", "dwt_plan_set_tile", "dwt_plan_get_scheme", "dwt_plan_set_normalization",
-    "dwt2_forward", "dwt2_inverse", "dwt2_forward_host", "dwt2_inverse_host", "dwt_batch_submit",
+    "dwt2_forward", "dwt2_inverse", "dwt2_forward_noalloc", "dwt2_forward_host", "dwt2_inverse_host", "dwt_batch_submit",
     "dwt_plan_device_status", "dwt_plan_set_profiling", "dwt_plan_read_profile", "dwt_plan_autotune",
     "dwt_plan_destroy", "dwt_status_string", "dwt_version", "Plan", "DwtRequest",
 ]
@@ -65,6 +65,9 @@ EXPORTS = {
                       ctypes.c_void_p], ctypes.c_int),
     "dwt2_inverse": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_size_t,
                       ctypes.c_void_p], ctypes.c_int),
+    "dwt2_forward_noalloc": ([ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                              ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_size_t,
+                              ctypes.c_void_p], ctypes.c_int),
     "dwt2_forward_host": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p,
                            ctypes.c_size_t, ctypes.c_void_p], ctypes.c_int),
     "dwt2_inverse_host": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p,
@@ -142,6 +145,14 @@ def dwt2_forward(plan: int, d_in: int, in_pitch: int, d_out: int, out_pitch: int
 
 def dwt2_inverse(plan: int, d_coef: int, coef_pitch: int, d_out: int, out_pitch: int, stream: int = 0) -> None:
     _check(lib().dwt2_inverse(plan, d_coef, coef_pitch, d_out, out_pitch, stream), "dwt2_inverse")
+
+
+def dwt2_forward_noalloc(w: int, h: int, wavelet: int, levels: int, dtype: int, d_in: int, in_pitch: int,
+                         d_out: int, out_pitch: int, stream: int = 0) -> None:
+    """Forward transform without a plan and without any device allocation
+    (scratch in a fixed 32 MiB device array of the library; see dwt.h)."""
+    _check(lib().dwt2_forward_noalloc(w, h, wavelet, levels, dtype, d_in, in_pitch, d_out, out_pitch, stream),
+           "dwt2_forward_noalloc")
 
 
 def dwt2_forward_host(plan: int, h_in: int, in_pitch: int, h_out: int, out_pitch: int, stream: int = 0) -> None:
