@@ -101,13 +101,14 @@ dwt_status dwt_plan_create(int w, int h, dwt_wavelet wavelet, int levels, dwt_dt
  * DWT_EUNSUPPORTED.  DWT_ROWCOL allocates a w x h intermediate plane. */
 dwt_status dwt_plan_set_scheme(dwt_plan plan, dwt_scheme scheme);
 
-/* Tile shape of the kernels (autotuner knobs).  min_strip_rows: the least
- * number of quadruple rows a warp streams (0 = default 2); a launch uses
- * longer strips when that still fills every SM once.  stages: depth of each
- * warp's shared-memory ring of row chunks, 1..4 (0 = default); deeper rings
- * keep more loads in flight per warp, shallower ones let more warps reside.
- * Errors: DWT_EINVAL for values out of range. */
-dwt_status dwt_plan_set_tile(dwt_plan plan, int min_strip_rows, int stages);
+/* Tile shape of the kernels (autotuner knobs).  strip_rows: target number
+ * of quadruple rows a warp streams (0 = default 10); a level too small to
+ * fill the GPU once with such strips uses shorter ones, down to 2 rows.
+ * stages: depth of each warp's shared-memory ring of row chunks, 1..4
+ * (0 = default 2); deeper rings keep more loads in flight per warp,
+ * shallower ones let more warps reside.  Errors: DWT_EINVAL for values out
+ * of range. */
+dwt_status dwt_plan_set_tile(dwt_plan plan, int strip_rows, int stages);
 
 /* The scheme a call will actually run (DWT_AUTO resolved). */
 dwt_status dwt_plan_get_scheme(dwt_plan plan, dwt_scheme* scheme);

@@ -33,7 +33,7 @@ constexpr int kQuadsPerLane =
 template <int SCHEME, int WL, typename ST, bool INV>
 using FusedCfg = Cfg<ST, float, typename FusedProgram<SCHEME, WL, INV>::type, INV ? SUBBANDS : SAMPLES,
                      INV ? SAMPLES : SUBBANDS, kQuadsPerLane<SCHEME, WL>, 8 / kQuadsPerLane<SCHEME, WL>,
-                     SCHEME == CONVOLUTION ? 2 : 4>;
+                     SCHEME == CONVOLUTION ? 8 : 16>;
 
 // The eight float combinations of one fused scheme.
 template <int SCHEME>

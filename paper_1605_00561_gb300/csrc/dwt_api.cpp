@@ -292,6 +292,16 @@ bool encode_2d(CUtensorMap* m, int dtype, const void* base, int w, int h, size_t
 
 size_t elem_size(int dtype) { return dtype == F16S ? 2 : 4; }
 
+// Quad rows per strip.  Strips of about ten rows keep several waves of
+// one-warp blocks in flight, so the block scheduler balances SMs that
+// progress at different rates, while the vertical halo re-reads hit L2
+// (vertically adjacent strips run at the same time).  A level too small to
+// fill one wave at that height gets shorter strips, down to two rows.
+int strip_height(int target, int ch, int ncs, int cap_warps) {
+  const long long one_wave = ((long long)ch * ncs + cap_warps - 1) / cap_warps;
+  return (int)std::max<long long>(2, std::min<long long>(target, one_wave));
+}
+
 size_t round_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 }  // namespace
@@ -330,7 +340,7 @@ struct dwt_plan_s {
   std::vector<ProfRec> pending;
   std::vector<cudaEvent_t> pool;
   int nstages = kDefaultStages;
-  int tmin = 2;
+  int strip_rows = kDefaultStripRows;
   std::mutex mu;
 };
 
@@ -465,8 +475,7 @@ dwt_status launch(dwt_plan_s* p, const LaunchKey& key, LevelArgs& a, const Coefs
   // one strip per resident warp when the level is large enough: a single
   // wave, with strips as tall as that allows (less vertical halo)
   a.ncs = (a.cw + ki.uq - 1) / ki.uq;
-  const int nrs_target = std::max(1, cap * kWarpsPerCta / a.ncs);
-  a.T = std::max(p->tmin, (a.ch + nrs_target - 1) / nrs_target);
+  a.T = strip_height(p->strip_rows, a.ch, a.ncs, cap);
   a.nrs = (a.ch + a.T - 1) / a.T;
   a.nstages = p->nstages;
   a.status = p->d_status;
@@ -744,8 +753,7 @@ dwt_status forward_on_scratch(int w, int h, int wavelet, int levels, int dtype, 
       per_sm = 1;
     const int cap = std::max(sms, 1) * std::max(per_sm, 1);
     a.ncs = (a.cw + ki.uq - 1) / ki.uq;
-    const int nrs_target = std::max(1, cap * kWarpsPerCta / a.ncs);
-    a.T = std::max(2, (a.ch + nrs_target - 1) / nrs_target);
+    a.T = strip_height(kDefaultStripRows, a.ch, a.ncs, cap);
     a.nrs = (a.ch + a.T - 1) / a.T;
     a.nstages = kDefaultStages;
     a.status = d_status;
@@ -843,11 +851,11 @@ dwt_status dwt_plan_set_scheme(dwt_plan p, dwt_scheme scheme) {
   return DWT_OK;
 }
 
-dwt_status dwt_plan_set_tile(dwt_plan p, int min_strip_rows, int stages) {
-  if (!p || min_strip_rows < 0 || min_strip_rows > 1 << 20 || stages < 0 || stages > kMaxStages)
+dwt_status dwt_plan_set_tile(dwt_plan p, int strip_rows, int stages) {
+  if (!p || strip_rows < 0 || strip_rows > 1 << 20 || stages < 0 || stages > kMaxStages)
     return DWT_EINVAL;
   std::lock_guard<std::mutex> lk(p->mu);
-  p->tmin = min_strip_rows ? min_strip_rows : 2;
+  p->strip_rows = strip_rows ? strip_rows : kDefaultStripRows;
   p->nstages = stages ? stages : kDefaultStages;
   return DWT_OK;
 }

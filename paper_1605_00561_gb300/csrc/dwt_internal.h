@@ -30,9 +30,10 @@ enum Pass : int {
   PASS_HORZ = 2     // row-column baseline: horizontal 1-D transform
 };
 
-constexpr int kWarpsPerCta = 4;  // independent warps (one strip each) per CTA
+constexpr int kWarpsPerCta = 1;  // independent warps (one strip each) per CTA
 constexpr int kMaxStages = 4;    // ring depth per warp
 constexpr int kDefaultStages = 2;
+constexpr int kDefaultStripRows = 10;
 
 // Lifting coefficients per predict/update pair and axis.  A coefficient of
 // an axis whose length is 1 is zero, which makes that axis' lifting the

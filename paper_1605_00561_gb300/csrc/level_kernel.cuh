@@ -74,7 +74,7 @@ __device__ __forceinline__ void copy_bytes(void* d, const void* s) {
 }
 
 template <typename ST_, typename VT_, class PROG_, int LOAD_, int STORE_, int QL_ = 4, int CH_ = 2,
-          int MINB_ = 4>
+          int MINW_ = 16>
 struct Cfg {
   using ST = ST_;
   using VT = VT_;
@@ -83,7 +83,7 @@ struct Cfg {
   static constexpr int LOAD = LOAD_, STORE = STORE_;
   static constexpr int QL = QL_;  // quadruples per lane
   static constexpr int CH = CH_;  // quad rows per ring stage
-  static constexpr int MIN_BLOCKS = MINB_;  // CTAs per SM the register budget must allow
+  static constexpr int MIN_WARPS = MINW_;  // warps per SM the register budget must allow
   static constexpr int WQ = 32 * QL;  // quadruple columns per warp
   // halo quads per side: covers the stencil reach and keeps each lane's
   // first quadruple a multiple of QL (aligned vector stores)
@@ -149,6 +149,59 @@ struct Strip {
     }
   }
 
+  // ---- border columns --------------------------------------------------------
+  // A strip whose columns leave the image still loads by TMA (the box reads
+  // zeros outside the tensor) when every mirrored value its halo needs lies
+  // inside the box.  The lanes holding such columns then read the mirrored
+  // shared-memory column instead of their own (load_row); in-image columns
+  // hold their true value whichever way the chunk was filled.  Columns
+  // further out never reach a stored coefficient; they read a clamped,
+  // in-box column.
+  __device__ __forceinline__ bool cols_inside() const {
+    if constexpr (C::LOAD == SAMPLES) return 2 * mfirst >= 0 && 2 * mfirst + C::SPAN <= a.W;
+    else return mfirst >= 0 && mfirst + C::WQ <= a.fw;
+  }
+  // box-relative index of the mirror of sample column x (SAMPLES) or of
+  // quad m of a plane of column parity px (SUBBANDS)
+  __device__ __forceinline__ int mirror_col(int x, int px) const {
+    if constexpr (C::LOAD == SAMPLES) {
+      return mirror(x, a.W) - align_down(2 * mfirst, C::A);
+    } else {
+      return (mirror(2 * x + px, a.W) >> 1) - align_down(mfirst, C::A);
+    }
+  }
+  __device__ __forceinline__ bool cols_by_tma() const {
+    if (cols_inside()) return true;
+    // the farthest halo element on each side must mirror into the box
+    if constexpr (C::LOAD == SAMPLES) {
+      const int lo = 2 * mfirst;
+      const int m_lo = lo < 0 ? mirror_col(lo, 0) : 0;
+      const int m_hi = lo + C::SPAN > a.W ? mirror_col(a.W + 2 * C::HQ, 0) : 0;
+      return m_lo >= 0 && m_lo < C::ROWE && m_hi >= 0 && m_hi < C::ROWE;
+    } else {
+      bool ok = true;
+#pragma unroll
+      for (int px = 0; px < 2; ++px) {
+        const int pw = px ? a.fw : a.cw;
+        if (mfirst < 0) {
+          const int s = mirror_col(mfirst, px);
+          ok = ok && s >= 0 && s < C::ROWE;
+        }
+        if (mfirst + C::WQ > pw) {
+          const int s = mirror_col(pw + C::HQ, px);
+          ok = ok && s >= 0 && s < C::ROWE;
+        }
+      }
+      return ok;
+    }
+  }
+  __device__ __forceinline__ bool chunk_by_tma(int c) const {
+    if (!a.src_tma || a.W < 2 || a.H < 2) return false;
+    const int y0 = yfirst + c * C::CH;
+    const bool rows = C::LOAD == SAMPLES ? (2 * y0 >= 0 && 2 * y0 + C::ROWS <= a.H)
+                                         : (y0 >= 0 && y0 + C::CH <= a.fh);
+    return rows && cols_by_tma();
+  }
   // ---- fills ---------------------------------------------------------------
   __device__ void fill(int c, int s) const {
     const int y0 = yfirst + c * C::CH;
@@ -157,8 +210,7 @@ struct Strip {
     const int col = lane_col();
     if constexpr (C::LOAD == SAMPLES) {
       const int sy0 = 2 * y0, xs = 2 * mfirst;
-      const bool inside = !tiny && sy0 >= 0 && sy0 + C::ROWS <= a.H && xs >= 0 && xs + C::SPAN <= a.W;
-      if (inside && a.src_tma) {
+      if (!tiny && a.src_tma && sy0 >= 0 && sy0 + C::ROWS <= a.H && cols_by_tma()) {
         if (lane == 0) {
           ptx::fence_proxy_async_smem();
           ptx::mbar_arrive_expect_tx(bar, C::BOX_BYTES);
@@ -206,8 +258,7 @@ struct Strip {
       ptx::mbar_arrive(bar);
     } else {
       // four subband planes; the lane covers quads mfirst + QL*lane + (0..QL-1)
-      const bool inside = !tiny && y0 >= 0 && y0 + C::CH <= a.fh && mfirst >= 0 && mfirst + C::WQ <= a.fw;
-      if (inside && a.src_tma) {
+      if (!tiny && a.src_tma && y0 >= 0 && y0 + C::CH <= a.fh && cols_by_tma()) {
         if (lane == 0) {
           ptx::fence_proxy_async_smem();
           ptx::mbar_arrive_expect_tx(bar, 4 * C::BOX_BYTES);
@@ -273,15 +324,34 @@ struct Strip {
   }
 
   // ---- consumer --------------------------------------------------------------
-  __device__ __forceinline__ Row<VT, QL> load_row(int s, int r) const {
+  // Border lanes: the shared-memory column each of the lane's elements
+  // reads (one byte per element, computed once per strip by remap_cols), and
+  // a mask of the elements too far out to reach any stored coefficient.
+  struct Remap {
+    bool on;
+    uint32_t col[2];
+    uint32_t zero;
+  };
+
+  __device__ __forceinline__ Row<VT, QL> load_row(int s, int r, const Remap& rm) const {
     Row<VT, QL> o;
     const int col = lane_col();
     if constexpr (C::LOAD == SAMPLES) {
       // row 2r: LL HL LL HL ..., row 2r+1: LH HH LH HH ...
       ST v0[2 * QL], v1[2 * QL];
-      const ST* p0 = plane(s, 0) + (2 * r) * C::ROWE + col;
-      copy_bytes<2 * QL * C::ES>(v0, p0);
-      copy_bytes<2 * QL * C::ES>(v1, p0 + C::ROWE);
+      const ST* p0 = plane(s, 0) + (2 * r) * C::ROWE;
+      if (!rm.on) {
+        copy_bytes<2 * QL * C::ES>(v0, p0 + col);
+        copy_bytes<2 * QL * C::ES>(v1, p0 + C::ROWE + col);
+      } else {
+#pragma unroll
+        for (int t = 0; t < 2 * QL; ++t) {
+          const int c = (rm.col[t / 4] >> (8 * (t % 4))) & 0xff;
+          const bool z = (rm.zero >> t) & 1;
+          v0[t] = z ? StoreT<ST>::from_v(VT(0)) : p0[c];
+          v1[t] = z ? StoreT<ST>::from_v(VT(0)) : p0[C::ROWE + c];
+        }
+      }
 #pragma unroll
       for (int j = 0; j < QL; ++j) {
         o.s[LL][j] = StoreT<ST>::to_v(v0[2 * j]);
@@ -293,12 +363,62 @@ struct Strip {
 #pragma unroll
       for (int p = 0; p < 4; ++p) {
         ST v[QL];
-        copy_bytes<QL * C::ES>(v, plane(s, p) + r * C::ROWE + col);
+        const ST* pr = plane(s, p) + r * C::ROWE;
+        if (!rm.on) {
+          copy_bytes<QL * C::ES>(v, pr + col);
+        } else {
+          const int px = p & 1;
+#pragma unroll
+          for (int t = 0; t < QL; ++t) {
+            const int c = (rm.col[px] >> (8 * t)) & 0xff;
+            const bool z = (rm.zero >> (QL * px + t)) & 1;
+            v[t] = z ? StoreT<ST>::from_v(VT(0)) : pr[c];
+          }
+        }
 #pragma unroll
         for (int j = 0; j < QL; ++j) o.s[p][j] = StoreT<ST>::to_v(v[j]);
       }
     }
     return o;
+  }
+
+  __device__ __forceinline__ Remap remap_cols() const {
+    Remap rm{false, {0u, 0u}, 0u};
+    if (a.W < 2 || a.H < 2 || !a.src_tma || cols_inside() || !cols_by_tma()) return rm;
+    if constexpr (C::LOAD == SAMPLES) {
+      const int xs = 2 * mfirst, xal = align_down(xs, C::A), x0 = xs + 2 * QL * lane;
+      rm.on = x0 < 0 || x0 + 2 * QL > a.W;
+      if (!rm.on) return rm;
+#pragma unroll
+      for (int t = 0; t < 2 * QL; ++t) {
+        const int x = x0 + t;
+        uint32_t c = 0;
+        if (x >= -2 * C::HQ && x <= a.W + 2 * C::HQ) c = (uint32_t)min(max(mirror(x, a.W) - xal, 0), C::ROWE - 1);
+        else rm.zero |= 1u << t;
+        rm.col[t / 4] |= c << (8 * (t % 4));
+      }
+    } else {
+      const int xal = align_down(mfirst, C::A), m = mfirst + QL * lane;
+      rm.on = m < 0 || m + QL > a.fw;
+      if (!rm.on) return rm;
+#pragma unroll
+      for (int px = 0; px < 2; ++px) {
+        const int pw = px ? a.fw : a.cw;
+#pragma unroll
+        for (int t = 0; t < QL; ++t) {
+          const int mm = m + t;
+          uint32_t c = 0;
+          if (mm >= -C::HQ && mm <= pw + C::HQ) {
+            const int sm_ = (mm >= 0 && mm < pw) ? mm : (mirror(2 * mm + px, a.W) >> 1);
+            c = (uint32_t)min(max(sm_ - xal, 0), C::ROWE - 1);
+          } else {
+            rm.zero |= 1u << (QL * px + t);
+          }
+          rm.col[px] |= c << (8 * t);
+        }
+      }
+    }
+    return rm;
   }
 
   // Per-lane output bases, computed once per strip.
@@ -383,15 +503,33 @@ struct Strip {
   }
 };
 
+// Strip order: the two border columns first (their halo handling makes
+// them the longest), then the interior row by row.  Blocks are dispatched
+// in this order, so the long strips start in the first wave.
+__device__ __forceinline__ void strip_coords(int s, int ncs, int nrs, int& cs, int& rs) {
+  if (ncs <= 2) {
+    cs = s % ncs;
+    rs = s / ncs;
+  } else if (s < 2 * nrs) {
+    cs = (s & 1) ? ncs - 1 : 0;
+    rs = s >> 1;
+  } else {
+    const int i = s - 2 * nrs;
+    cs = 1 + i % (ncs - 2);
+    rs = i / (ncs - 2);
+  }
+}
+
 template <class C>
-__global__ void __launch_bounds__(kWarpsPerCta * 32, C::MIN_BLOCKS)
+__global__ void __launch_bounds__(kWarpsPerCta * 32, C::MIN_WARPS / kWarpsPerCta)
     level_kernel(const __grid_constant__ TmaMaps maps, const __grid_constant__ LevelArgs a,
                  const __grid_constant__ Coefs cf, const __grid_constant__ ConvTaps ct) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int strip = blockIdx.x * kWarpsPerCta + warp;
   if (strip >= a.ncs * a.nrs) return;  // whole warp: no CTA-wide synchronisation is used
-  const int cs = strip % a.ncs, rs = strip / a.ncs;
+  int cs, rs;
+  strip_coords(strip, a.ncs, a.nrs, cs, rs);
   const int q0 = rs * a.T;
   const int rows_out = min(a.T, a.ch - q0);
   if (rows_out <= 0) return;
@@ -416,6 +554,7 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, C::MIN_BLOCKS)
   for (int c = 0; c < NS - 1 && c < nchunks; ++c) sp.fill(c, c);
 
   const typename Strip<C>::Out ob = sp.out_bases();
+  const typename Strip<C>::Remap remap = sp.remap_cols();
   Pipe<typename C::VT, C::QL, typename C::PROG> pipe;
   pipe.reset();
   for (int c = 0; c < nchunks; ++c) {
@@ -440,7 +579,7 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, C::MIN_BLOCKS)
     // and the loop body stays small enough for the instruction cache
 #pragma unroll 2
     for (int r = 0; r < C::CH; ++r) {
-      const Row<typename C::VT, C::QL> in = sp.load_row(s, r);
+      const Row<typename C::VT, C::QL> in = sp.load_row(s, r, remap);
       const Row<typename C::VT, C::QL> out = pipe.push(in, cf, ct);
       const int q = qc + r;
       if (q >= q0 && q < q_end) sp.store_row(ob, out, q);

@@ -175,6 +175,8 @@ struct Lin {
                                 VS::lo <= 0 && VS::hi >= 0 && HS::lo <= 0 && HS::hi >= 0;
         if constexpr (centre == CENTRE_PASS) {
           float s[QL];
+#pragma unroll
+          for (int j = 0; j < QL; ++j) s[j] = 0.0f;  // overwritten by the first tap
           bool first = true;
           static_for<VS::lo, VS::hi>([&](auto dy) {
             constexpr int DY = decltype(dy)::value;

@@ -125,8 +125,8 @@ def dwt_plan_set_scheme(plan: int, scheme: int) -> None:
     _check(lib().dwt_plan_set_scheme(plan, scheme), "dwt_plan_set_scheme")
 
 
-def dwt_plan_set_tile(plan: int, min_strip_rows: int = 0, stages: int = 0) -> None:
-    _check(lib().dwt_plan_set_tile(plan, min_strip_rows, stages), "dwt_plan_set_tile")
+def dwt_plan_set_tile(plan: int, strip_rows: int = 0, stages: int = 0) -> None:
+    _check(lib().dwt_plan_set_tile(plan, strip_rows, stages), "dwt_plan_set_tile")
 
 
 def dwt_plan_get_scheme(plan: int) -> int:
