@@ -540,11 +540,16 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, C::MIN_WARPS / kWarpsPerCta
               smem_raw + (size_t)warp * NS * C::STAGE_BYTES,
               reinterpret_cast<uint64_t*>(smem_raw + (size_t)kWarpsPerCta * NS * C::STAGE_BYTES) +
                   warp * kMaxStages};
+  ptx::launch_dependents();
   if (lane == 0) {
     for (int s = 0; s < NS; ++s) ptx::mbar_init(&sp.bars[s], 32);
     ptx::fence_barrier_init();
+    if (a.src_tma) ptx::prefetch_tensormap(&maps.m[0]);
   }
   __syncwarp();
+  // the previous level's kernel may still be running: every read and write
+  // of level data comes after this point
+  ptx::wait_prerequisites();
 
   // rows streamed: the strip plus its halo, padded to whole chunks (the
   // extra rows are mirrored image rows, lifted but never stored)
@@ -623,9 +628,19 @@ struct Instance {
       configured[dev] = 1;
     }
     const long long strips = (long long)a.ncs * a.nrs;
-    dim3 grid((unsigned)((strips + kWarpsPerCta - 1) / kWarpsPerCta));
-    level_kernel<C><<<grid, kWarpsPerCta * 32, bytes, s>>>(m, a, cf, ct);
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)((strips + kWarpsPerCta - 1) / kWarpsPerCta));
+    cfg.blockDim = dim3(kWarpsPerCta * 32);
+    cfg.dynamicSmemBytes = bytes;
+    cfg.stream = s;
+    // programmatic dependent launch: this grid's blocks may start while the
+    // previous kernel in the stream finishes (they wait before reading)
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, level_kernel<C>, m, a, cf, ct);
   }
 };
 

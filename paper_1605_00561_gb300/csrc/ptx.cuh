@@ -105,5 +105,17 @@ __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.wait_all;" ::: "memory");
 }
 
+// Programmatic dependent launch: let the next kernel in the stream start its
+// blocks once every block of this grid is running, and, in that next
+// kernel, wait for this grid to complete (and its writes to be visible)
+// before touching the data it produced.  Both are no-ops for a launch
+// without the programmatic-serialisation attribute.
+__device__ __forceinline__ void launch_dependents() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+__device__ __forceinline__ void wait_prerequisites() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
 }  // namespace ptx
 }  // namespace dwt
