@@ -162,12 +162,22 @@ dwt_status dwt2_inverse_host(dwt_plan plan, const void* h_coef, size_t coef_pitc
                              void* h_out, size_t out_pitch_bytes, dwt_stream stream);
 
 /* Many transforms in one persistent launch.  Each request names a plan, its
- * device buffers and a direction; different sizes, level counts, wavelets
- * and dtypes may be mixed.  The kernel pulls (image, level, strip) work
- * items from a global queue; a level's strips wait, with a bounded spin,
- * for the previous level of the same image.  d_status (device memory, n
- * ints, may be NULL) receives per request DWT_OK or DWT_ETIMEOUT.  A plan
- * may appear at most once per call (DWT_EBUSY otherwise). */
+ * device buffers and a direction; different sizes, level counts, wavelets,
+ * dtypes and directions may be mixed.  Every level of every request runs
+ * in one kernel: persistent one-warp blocks pull (image, level, strip) work
+ * items from a global queue, ordered level-major across the requests, and
+ * a level's strips wait, with a bounded spin, until the previous level of
+ * the same image is done.  The scheme is fixed per dtype whatever the plan
+ * selects: Monolithic* (Sec. 4) for float32 and float16 storage, the
+ * separable JPEG 2000 lifting order for reversible int32 5/3; the plans'
+ * normalisation and strip height apply.  d_status (device memory, n ints,
+ * may be NULL) is cleared and then receives DWT_ETIMEOUT for any request
+ * whose wait or copy gave up.  A plan may appear at most once per call
+ * (DWT_EBUSY otherwise); outputs may not overlap each other or any input
+ * (DWT_EINVAL).  The call uploads its work list from page-locked memory
+ * and allocates its device work area stream-ordered; it synchronises with
+ * the previous batch's upload on the same device, so it cannot be captured
+ * into a CUDA graph. */
 typedef struct {
   dwt_plan plan;
   const void* in;

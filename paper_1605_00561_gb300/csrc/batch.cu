@@ -1,0 +1,195 @@
+// The persistent batch kernel behind dwt_batch_submit: many transforms of
+// mixed sizes, level counts, wavelets, storage types and directions in one
+// launch.
+//
+// Work items are (request, step, strip) triples, ordered step-major across
+// requests (a forward request's step j is level j; an inverse request's step
+// j is level L-1-j).  Persistent one-warp blocks pop items from a global
+// counter.  A strip of step j of a request first waits until every strip of
+// step j-1 of the same request is done (its input is that step's output);
+// items are popped in step order, so the awaited strips were all taken
+// earlier by running warps and the wait ends.  The wait is bounded: when it
+// runs out the request's status becomes DWT_ETIMEOUT and the strip is
+// skipped, never a hang.  Each kind of request runs the same strip code as
+// the per-level kernels (run_strip), with a fixed scheme: Monolithic* for
+// the float wavelets, the separable JPEG 2000 order for reversible 5/3.
+#include "batch.h"
+#include "dispatch.cuh"
+
+namespace dwt {
+namespace dev {
+namespace {
+
+template <int WL, typename ST, bool INV>
+using FloatKind = FusedCfg<MONOLITHIC_S, WL, ST, INV>;
+template <bool INV>
+using IntKind = Cfg<int, int, typename IntFused<INV>::type, INV ? SUBBANDS : SAMPLES, INV ? SAMPLES : SUBBANDS>;
+
+// The kinds a batch can hold, in BatchKind order.
+using K0 = FloatKind<W97, float, false>;
+using K1 = FloatKind<W97, float, true>;
+using K2 = FloatKind<W53, float, false>;
+using K3 = FloatKind<W53, float, true>;
+using K4 = IntKind<false>;
+using K5 = IntKind<true>;
+using K6 = FloatKind<W97, __half, false>;
+using K7 = FloatKind<W97, __half, true>;
+using K8 = FloatKind<W53, __half, false>;
+using K9 = FloatKind<W53, __half, true>;
+
+constexpr int cmax_bytes(int a, int b) { return a > b ? a : b; }
+constexpr int kStageStride =
+    cmax_bytes(cmax_bytes(cmax_bytes(K0::STAGE_BYTES, K1::STAGE_BYTES), cmax_bytes(K2::STAGE_BYTES, K3::STAGE_BYTES)),
+               cmax_bytes(cmax_bytes(K4::STAGE_BYTES, K5::STAGE_BYTES),
+                          cmax_bytes(cmax_bytes(K6::STAGE_BYTES, K7::STAGE_BYTES),
+                                     cmax_bytes(K8::STAGE_BYTES, K9::STAGE_BYTES))));
+constexpr uint32_t kDepSpins = 1u << 22;  // x ~0.1-1 us of nanosleep: seconds at most
+
+__constant__ ConvTaps kNoTaps;  // none of the batch kinds reads taps
+
+// One strip of one level.  Not inlined: each kind gets its own register
+// allocation instead of the union of all ten.
+template <class C>
+__device__ __noinline__ bool go(const BatchLevel& L, int strip, unsigned char* ring, uint64_t* bars,
+                                uint32_t& ctr) {
+  if (L.a.src_tma) {
+    // the maps were uploaded by a copy, and an earlier batch may have left
+    // another map at the same address in the tensor-map cache
+    constexpr int nmaps = C::LOAD == SAMPLES ? 1 : 4;
+    for (int i = 0; i < nmaps; ++i) ptx::fence_tensormap_acquire(&L.maps.m[i]);
+  }
+  return run_strip<C>(L.a, L.maps, L.cf, kNoTaps, strip, ring, kStageStride, bars, ctr);
+}
+
+__device__ __forceinline__ bool dispatch(const BatchLevel& L, int strip, unsigned char* ring, uint64_t* bars,
+                                         uint32_t& ctr) {
+  switch (L.kind) {
+    case BK_97_F32_FWD: return go<K0>(L, strip, ring, bars, ctr);
+    case BK_97_F32_INV: return go<K1>(L, strip, ring, bars, ctr);
+    case BK_53_F32_FWD: return go<K2>(L, strip, ring, bars, ctr);
+    case BK_53_F32_INV: return go<K3>(L, strip, ring, bars, ctr);
+    case BK_53_I32_FWD: return go<K4>(L, strip, ring, bars, ctr);
+    case BK_53_I32_INV: return go<K5>(L, strip, ring, bars, ctr);
+    case BK_97_F16_FWD: return go<K6>(L, strip, ring, bars, ctr);
+    case BK_97_F16_INV: return go<K7>(L, strip, ring, bars, ctr);
+    case BK_53_F16_FWD: return go<K8>(L, strip, ring, bars, ctr);
+    case BK_53_F16_INV: return go<K9>(L, strip, ring, bars, ctr);
+  }
+  return false;
+}
+
+__device__ __forceinline__ int load_acquire(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// 12 resident one-warp blocks per SM leave 168 registers a thread, enough
+// for every kind without spills.
+__global__ void __launch_bounds__(32, 12) batch_kernel(const __grid_constant__ BatchParams P) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  const int lane = threadIdx.x & 31;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + (size_t)kBatchStages * kStageStride);
+  if (lane == 0) {
+    for (int s = 0; s < kBatchStages; ++s) ptx::mbar_init(&bars[s], 32);
+    ptx::fence_barrier_init();
+  }
+  __syncwarp();
+  uint32_t chunk_ctr = 0;
+  for (;;) {
+    int it = 0;
+    if (lane == 0) it = atomicAdd(P.head, 1);
+    it = __shfl_sync(kFull, it, 0);
+    if (it >= P.nitems) break;
+    const BatchItem item = P.items[it];
+    const BatchLevel& L = P.levels[item.level];
+    bool ok = true;
+    if (L.dep >= 0) {
+      if (lane == 0) {
+        const int need = P.levels[L.dep].nstrips;
+        uint32_t spins = 0;
+        while (load_acquire(&P.done[L.dep]) < need) {
+          if (++spins > kDepSpins) {
+            ok = false;
+            break;
+          }
+          __nanosleep(128);
+        }
+        __threadfence();
+      }
+      ok = __shfl_sync(kFull, ok ? 1 : 0, 0) != 0;
+      // every lane acquires the producers' writes for itself (the ping-pong
+      // LL scratch is rewritten within one launch, so no line this SM read
+      // earlier may be reused), then orders them before its TMA reads
+      // (async proxy)
+      (void)load_acquire(&P.done[L.dep]);
+      ptx::fence_proxy_async_global();
+    }
+    if (ok) ok = dispatch(L, item.strip, smem_raw, bars, chunk_ctr);
+    if (!ok && lane == 0) atomicExch(&P.req_status[L.request], 5 /* DWT_ETIMEOUT */);
+    // publish this strip: the warp's stores, then one release by lane 0
+    __syncwarp();
+    if (lane == 0) {
+      __threadfence();
+      atomicAdd(&P.done[item.level], 1);
+    }
+  }
+}
+
+template <class C>
+void kind_info(KernelInfo* k) {
+  *k = KernelInfo{};
+  k->hq = C::HQ;
+  k->uq = C::UQ;
+  k->up = C::Tot::UP;
+  k->down = C::Tot::DOWN;
+  k->load = (Layout)C::LOAD;
+  k->store = (Layout)C::STORE;
+  k->box_w = C::ROWE;
+  k->box_h = C::ROWS;
+  k->smem_bytes = batch_smem_bytes();
+  k->fn = reinterpret_cast<const void*>(&batch_kernel);
+  k->supported = true;
+}
+
+}  // namespace
+}  // namespace dev
+
+bool batch_kind_info(int kind, KernelInfo* k) {
+  using namespace dev;
+  switch (kind) {
+    case BK_97_F32_FWD: kind_info<K0>(k); return true;
+    case BK_97_F32_INV: kind_info<K1>(k); return true;
+    case BK_53_F32_FWD: kind_info<K2>(k); return true;
+    case BK_53_F32_INV: kind_info<K3>(k); return true;
+    case BK_53_I32_FWD: kind_info<K4>(k); return true;
+    case BK_53_I32_INV: kind_info<K5>(k); return true;
+    case BK_97_F16_FWD: kind_info<K6>(k); return true;
+    case BK_97_F16_INV: kind_info<K7>(k); return true;
+    case BK_53_F16_FWD: kind_info<K8>(k); return true;
+    case BK_53_F16_INV: kind_info<K9>(k); return true;
+  }
+  return false;
+}
+
+size_t batch_smem_bytes() {
+  return (size_t)kBatchStages * dev::kStageStride + (size_t)kMaxStages * 8;
+}
+
+const void* batch_kernel_fn() { return reinterpret_cast<const void*>(&dev::batch_kernel); }
+
+cudaError_t launch_batch(const BatchParams& p, int blocks, cudaStream_t s) {
+  static int configured[64] = {0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev >= 0 && dev < 64 && !configured[dev]) {
+    cudaError_t e = cudaFuncSetAttribute(&dev::batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)batch_smem_bytes());
+    if (e != cudaSuccess) return e;
+    configured[dev] = 1;
+  }
+  dev::batch_kernel<<<blocks, 32, batch_smem_bytes(), s>>>(p);
+  return cudaGetLastError();
+}
+
+}  // namespace dwt

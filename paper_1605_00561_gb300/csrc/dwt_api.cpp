@@ -15,6 +15,7 @@
 #include <string>
 #include <vector>
 
+#include "batch.h"
 #include "dwt_internal.h"
 
 using namespace dwt;
@@ -530,9 +531,67 @@ dwt_status ensure_tmp(dwt_plan_s* p) {
   return from_cuda(cudaMalloc(&p->tmp, p->tmp_pitch * p->h));
 }
 
-// The transform proper: levels in order (forward) or reverse (inverse).
-dwt_status run(dwt_plan_s* p, bool inverse, const void* src, size_t src_pitch, void* dst,
-               size_t dst_pitch, cudaStream_t s) {
+// Where level k of a transform reads and writes (Mallat layout): the four
+// subband planes inside the coefficient buffer, with LL in the plan's
+// scratch except at the coarsest level, and the level's sample plane (the
+// image at level 0, the finer level's LL scratch above).
+struct LevelIO {
+  const void* band[4];
+  long long bpitch[4];
+  const void* samples;
+  long long spitch;
+};
+
+LevelIO level_io(const dwt_plan_s* p, bool inverse, int k, const LevelArgs& a, const void* src,
+                 size_t src_pitch, const void* dst, size_t dst_pitch) {
+  const size_t es = p->es;
+  LevelIO io;
+  const void* coef = inverse ? src : dst;
+  const size_t cp = inverse ? src_pitch : dst_pitch;
+  const char* cb = static_cast<const char*>(coef);
+  io.band[1] = cb + a.cw * es;
+  io.band[2] = cb + a.ch * cp;
+  io.band[3] = cb + a.ch * cp + a.cw * es;
+  for (int i = 1; i < 4; ++i) io.bpitch[i] = (long long)(cp / es);
+  if (k == p->levels - 1) {
+    io.band[0] = coef;
+    io.bpitch[0] = (long long)(cp / es);
+  } else {
+    io.band[0] = p->scratch[k & 1];
+    io.bpitch[0] = (long long)(p->scratch_pitch / es);
+  }
+  if (k == 0) {
+    io.samples = inverse ? dst : src;
+    io.spitch = (long long)((inverse ? dst_pitch : src_pitch) / es);
+  } else {
+    io.samples = p->scratch[(k - 1) & 1];
+    io.spitch = (long long)(p->scratch_pitch / es);
+  }
+  return io;
+}
+
+// Sources and destinations of one fused (single-launch) level.
+void fused_io(const LevelIO& io, bool inverse, LevelArgs& a) {
+  if (!inverse) {
+    a.src[0] = io.samples;
+    a.src_pitch[0] = io.spitch;
+    for (int i = 0; i < 4; ++i) {
+      a.dst[i] = const_cast<void*>(io.band[i]);
+      a.dst_pitch[i] = io.bpitch[i];
+    }
+  } else {
+    for (int i = 0; i < 4; ++i) {
+      a.src[i] = io.band[i];
+      a.src_pitch[i] = io.bpitch[i];
+    }
+    a.dst[0] = const_cast<void*>(io.samples);
+    a.dst_pitch[0] = io.spitch;
+  }
+}
+
+// Checks shared by every call that transforms one image with a plan.
+dwt_status check_buffers(const dwt_plan_s* p, const void* src, size_t src_pitch, const void* dst,
+                         size_t dst_pitch) {
   const size_t es = p->es;
   if (src_pitch < (size_t)p->w * es || dst_pitch < (size_t)p->w * es || src_pitch % es ||
       dst_pitch % es)
@@ -544,6 +603,15 @@ dwt_status run(dwt_plan_s* p, bool inverse, const void* src, size_t src_pitch, v
   if (overlaps(src, nsrc, dst, ndst)) return DWT_EINVAL;
   int cur = -1;
   if (cudaGetDevice(&cur) != cudaSuccess || cur != p->device) return DWT_EINVAL;
+  return DWT_OK;
+}
+
+// The transform proper: levels in order (forward) or reverse (inverse).
+dwt_status run(dwt_plan_s* p, bool inverse, const void* src, size_t src_pitch, void* dst,
+               size_t dst_pitch, cudaStream_t s) {
+  const size_t es = p->es;
+  const dwt_status chk = check_buffers(p, src, src_pitch, dst, dst_pitch);
+  if (chk != DWT_OK) return chk;
   p->last_stream = s;
   if (p->levels == 0)
     return from_cuda(cudaMemcpy2DAsync(dst, dst_pitch, src, src_pitch, (size_t)p->w * es, p->h,
@@ -561,35 +629,11 @@ dwt_status run(dwt_plan_s* p, bool inverse, const void* src, size_t src_pitch, v
     const int k = inverse ? Lv - 1 - step : step;
     LevelArgs a{};
     level_dims(p, k, a);
-    // the four subband planes of this level inside the Mallat-packed buffer
-    const void* coef = inverse ? src : dst;
-    const size_t cp = inverse ? src_pitch : dst_pitch;
-    const char* cb = static_cast<const char*>(coef);
-    const void* band[4];
-    long long bpitch[4];
-    band[1] = cb + a.cw * es;
-    band[2] = cb + a.ch * cp;
-    band[3] = cb + a.ch * cp + a.cw * es;
-    for (int i = 1; i < 4; ++i) bpitch[i] = (long long)(cp / es);
-    // LL of this level: the next level's input (scratch) or, at the last
-    // level, the top-left quadrant of the coefficient buffer
-    if (k == Lv - 1) {
-      band[0] = coef;
-      bpitch[0] = (long long)(cp / es);
-    } else {
-      band[0] = p->scratch[k & 1];
-      bpitch[0] = (long long)(p->scratch_pitch / es);
-    }
-    // the level's sample plane: image (level 0) or scratch
-    const void* samples;
-    long long spitch;
-    if (k == 0) {
-      samples = inverse ? dst : src;
-      spitch = (long long)((inverse ? dst_pitch : src_pitch) / es);
-    } else {
-      samples = p->scratch[(k - 1) & 1];
-      spitch = (long long)(p->scratch_pitch / es);
-    }
+    const LevelIO io = level_io(p, inverse, k, a, src, src_pitch, dst, dst_pitch);
+    const void* const* band = io.band;
+    const long long* bpitch = io.bpitch;
+    const void* samples = io.samples;
+    const long long spitch = io.spitch;
     const Coefs cf = make_coefs(L, p->norm, a.W, a.H, PASS_FUSED, inverse);
     ConvTaps ct;
     std::memset(&ct, 0, sizeof ct);
@@ -598,21 +642,7 @@ dwt_status run(dwt_plan_s* p, bool inverse, const void* src, size_t src_pitch, v
     dwt_status st;
     if (scheme != DWT_ROWCOL) {
       LaunchKey key{p->wavelet, p->dtype, scheme, PASS_FUSED, inverse ? 1 : 0};
-      if (!inverse) {
-        a.src[0] = samples;
-        a.src_pitch[0] = spitch;
-        for (int i = 0; i < 4; ++i) {
-          a.dst[i] = const_cast<void*>(band[i]);
-          a.dst_pitch[i] = bpitch[i];
-        }
-      } else {
-        for (int i = 0; i < 4; ++i) {
-          a.src[i] = band[i];
-          a.src_pitch[i] = bpitch[i];
-        }
-        a.dst[0] = const_cast<void*>(samples);
-        a.dst_pitch[0] = spitch;
-      }
+      fused_io(io, inverse, a);
       std::snprintf(slot, sizeof slot, "%s/L%d", inverse ? "inv" : "fwd", k);
       st = launch(p, key, a, cf, ct, s, slot);
     } else {
@@ -660,6 +690,180 @@ dwt_status run(dwt_plan_s* p, bool inverse, const void* src, size_t src_pitch, v
     if (st != DWT_OK) return st;
   }
   return DWT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Batches: every level of every request in one persistent launch (batch.cu)
+// ---------------------------------------------------------------------------
+int batch_kind(int wavelet, int dtype, bool inverse) {
+  const int inv = inverse ? 1 : 0;
+  if (dtype == DWT_F32 && wavelet == DWT_CDF97) return BK_97_F32_FWD + inv;
+  if (dtype == DWT_F32 && wavelet == DWT_CDF53) return BK_53_F32_FWD + inv;
+  if (dtype == DWT_I32 && wavelet == DWT_CDF53) return BK_53_I32_FWD + inv;
+  if (dtype == DWT_F16S && wavelet == DWT_CDF97) return BK_97_F16_FWD + inv;
+  if (dtype == DWT_F16S && wavelet == DWT_CDF53) return BK_53_F16_FWD + inv;
+  return -1;
+}
+
+// Page-locked upload buffer for the descriptors, one per device.  A new
+// batch refills it only after the previous upload out of it completed.
+struct BatchStaging {
+  std::mutex mu;
+  void* host = nullptr;
+  size_t cap = 0;
+  cudaEvent_t uploaded = nullptr;
+};
+BatchStaging g_staging[64];
+
+dwt_status batch_submit(const dwt_request* reqs, int n, cudaStream_t s, int* d_status) {
+  int device = -1;
+  if (cudaGetDevice(&device) != cudaSuccess) return DWT_ECUDA;
+  if (device < 0 || device >= 64) return DWT_EUNSUPPORTED;
+  std::vector<int> kinds(n);
+  int maxl = 0;
+  for (int i = 0; i < n; ++i) {
+    const dwt_plan_s* p = reqs[i].plan;
+    if (p->device != device) return DWT_EINVAL;
+    const dwt_status chk = check_buffers(p, reqs[i].in, reqs[i].in_pitch, reqs[i].out, reqs[i].out_pitch);
+    if (chk != DWT_OK) return chk;
+    kinds[i] = batch_kind(p->wavelet, p->dtype, reqs[i].inverse != 0);
+    if (kinds[i] < 0) return DWT_EUNSUPPORTED;
+    maxl = std::max(maxl, p->levels);
+  }
+  // images may not share memory with each other either
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < i; ++j) {
+      const dwt_plan_s *p = reqs[i].plan, *q = reqs[j].plan;
+      const size_t ni = plane_extent(p->w, p->h, reqs[i].out_pitch, p->es);
+      const size_t nj = plane_extent(q->w, q->h, reqs[j].out_pitch, q->es);
+      const size_t ii = plane_extent(p->w, p->h, reqs[i].in_pitch, p->es);
+      const size_t ij = plane_extent(q->w, q->h, reqs[j].in_pitch, q->es);
+      if (overlaps(reqs[i].out, ni, reqs[j].out, nj) || overlaps(reqs[i].out, ni, reqs[j].in, ij) ||
+          overlaps(reqs[j].out, nj, reqs[i].in, ii))
+        return DWT_EINVAL;
+    }
+
+  KernelInfo kinfo[BK_COUNT];
+  for (int k = 0; k < BK_COUNT; ++k)
+    if (!batch_kind_info(k, &kinfo[k])) return DWT_EUNSUPPORTED;
+  const Occ oc = occupancy(kinfo[0], device);
+  const int resident = oc.sms * oc.per_sm;
+
+  // levels in queue order: step-major across requests, so that every strip
+  // a level waits for sits earlier in the queue
+  std::vector<BatchLevel> levels;
+  std::vector<int> last_of(n, -1);
+  size_t nitems = 0;
+  for (int step = 0; step < maxl; ++step) {
+    int active = 0;
+    for (int i = 0; i < n; ++i) active += reqs[i].plan->levels > step;
+    const int cap = std::max(1, resident / std::max(active, 1));
+    for (int i = 0; i < n; ++i) {
+      const dwt_plan_s* p = reqs[i].plan;
+      if (p->levels <= step) continue;
+      const bool inverse = reqs[i].inverse != 0;
+      const int k = inverse ? p->levels - 1 - step : step;
+      const KernelInfo& ki = kinfo[kinds[i]];
+      BatchLevel b;
+      std::memset(&b, 0, sizeof b);
+      LevelArgs& a = b.a;
+      level_dims(p, k, a);
+      const LevelIO io = level_io(p, inverse, k, a, reqs[i].in, reqs[i].in_pitch, reqs[i].out,
+                                  reqs[i].out_pitch);
+      fused_io(io, inverse, a);
+      a.ncs = (a.cw + ki.uq - 1) / ki.uq;
+      a.T = strip_height(p->strip_rows, a.ch, a.ncs, cap);
+      a.nrs = (a.ch + a.T - 1) / a.T;
+      a.nstages = kBatchStages;
+      a.src_tma = 0;
+      if (a.W >= 2 && a.H >= 2) {
+        if (ki.load == SAMPLES) {
+          a.src_tma = encode_2d(&b.maps.m[0], p->dtype, a.src[0], a.W, a.H,
+                                (size_t)a.src_pitch[0] * p->es, ki.box_w, ki.box_h);
+        } else {
+          const int pw[4] = {a.cw, a.fw, a.cw, a.fw}, ph[4] = {a.ch, a.ch, a.fh, a.fh};
+          bool ok = true;
+          for (int j = 0; j < 4 && ok; ++j)
+            ok = encode_2d(&b.maps.m[j], p->dtype, a.src[j], pw[j], ph[j], (size_t)a.src_pitch[j] * p->es,
+                           ki.box_w, ki.box_h);
+          a.src_tma = ok;
+        }
+      }
+      b.cf = make_coefs(lifting_of(p->wavelet), p->norm, a.W, a.H, PASS_FUSED, inverse);
+      b.kind = kinds[i];
+      b.request = i;
+      b.nstrips = a.ncs * a.nrs;
+      b.dep = last_of[i];
+      last_of[i] = (int)levels.size();
+      nitems += (size_t)b.nstrips;
+      levels.push_back(b);
+    }
+  }
+  if (nitems > (size_t)INT32_MAX) return DWT_EINVAL;
+  const int nl = (int)levels.size();
+
+  // device block: levels | items | head | done[nl] | status[n]
+  const size_t off_items = round_up(sizeof(BatchLevel) * nl, 256);
+  const size_t off_head = round_up(off_items + sizeof(BatchItem) * nitems, 256);
+  const size_t upload = off_head;
+  const size_t counters = sizeof(int) * (1 + (size_t)nl + (size_t)n);
+  BatchStaging& st = g_staging[device];
+  std::lock_guard<std::mutex> lk(st.mu);
+  cudaError_t e = cudaSuccess;
+  if (!st.uploaded) e = cudaEventCreateWithFlags(&st.uploaded, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventSynchronize(st.uploaded);
+  if (e == cudaSuccess && st.cap < upload) {
+    if (st.host) cudaFreeHost(st.host);
+    st.host = nullptr;
+    st.cap = 0;
+    e = cudaMallocHost(&st.host, upload * 2);
+    if (e == cudaSuccess) st.cap = upload * 2;
+  }
+  if (e != cudaSuccess) return from_cuda(e);
+  // requests without levels are copies
+  for (int i = 0; i < n && e == cudaSuccess; ++i) {
+    const dwt_plan_s* p = reqs[i].plan;
+    if (p->levels == 0)
+      e = cudaMemcpy2DAsync(reqs[i].out, reqs[i].out_pitch, reqs[i].in, reqs[i].in_pitch,
+                            (size_t)p->w * p->es, p->h, cudaMemcpyDeviceToDevice, s);
+  }
+  if (e == cudaSuccess && d_status && n) e = cudaMemsetAsync(d_status, 0, sizeof(int) * n, s);
+  if (e != cudaSuccess || nitems == 0) return from_cuda(e);
+
+  // tensor maps read from global memory must be 64-byte aligned
+  unsigned char* block = nullptr;
+  e = cudaMallocAsync(reinterpret_cast<void**>(&block), upload + counters + 128, s);
+  if (e != cudaSuccess) return from_cuda(e);
+  unsigned char* d = block + ((128 - (reinterpret_cast<uintptr_t>(block) & 127)) & 127);
+  int* head = reinterpret_cast<int*>(d + off_head);
+  int* done = head + 1;
+  // a strip that gives up on its ring raises its level's status word: the
+  // caller's slot for the request, or a slot of this block
+  int* status = d_status ? d_status : done + nl;
+  for (int l = 0; l < nl; ++l) levels[l].a.status = status + levels[l].request;
+  unsigned char* h = static_cast<unsigned char*>(st.host);
+  std::memcpy(h, levels.data(), sizeof(BatchLevel) * nl);
+  BatchItem* items = reinterpret_cast<BatchItem*>(h + off_items);
+  size_t it = 0;
+  for (int l = 0; l < nl; ++l)
+    for (int sidx = 0; sidx < levels[l].nstrips; ++sidx) items[it++] = BatchItem{l, sidx};
+  e = cudaMemcpyAsync(d, h, upload, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaEventRecord(st.uploaded, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(head, 0, counters, s);
+  if (e == cudaSuccess) {
+    BatchParams bp;
+    bp.levels = reinterpret_cast<const BatchLevel*>(d);
+    bp.items = reinterpret_cast<const BatchItem*>(d + off_items);
+    bp.nitems = (int)nitems;
+    bp.head = head;
+    bp.done = done;
+    bp.req_status = status;
+    e = launch_batch(bp, (int)std::min<size_t>((size_t)resident, nitems), s);
+  }
+  const cudaError_t ef = cudaFreeAsync(block, s);
+  if (e == cudaSuccess) e = ef;
+  for (int i = 0; i < n; ++i) reqs[i].plan->last_stream = s;
+  return from_cuda(e);
 }
 
 struct DeviceGuard {
@@ -923,21 +1127,21 @@ dwt_status dwt2_inverse_host(dwt_plan p, const void* h_coef, size_t coef_pitch, 
 
 dwt_status dwt_batch_submit(const dwt_request* reqs, int n, dwt_stream stream, int* d_status) {
   if (n < 0 || (n > 0 && !reqs)) return DWT_EINVAL;
+  std::vector<dwt_plan_s*> plans(n);
   for (int i = 0; i < n; ++i) {
     if (!reqs[i].plan) return DWT_EINVAL;
-    for (int j = 0; j < i; ++j)
-      if (reqs[j].plan == reqs[i].plan) return DWT_EBUSY;
+    plans[i] = reqs[i].plan;
   }
-  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  for (int i = 0; i < n; ++i) {
-    dwt_plan p = reqs[i].plan;
-    std::lock_guard<std::mutex> lk(p->mu);
-    dwt_status st = run(p, reqs[i].inverse != 0, reqs[i].in, reqs[i].in_pitch, reqs[i].out,
-                        reqs[i].out_pitch, s);
-    if (st != DWT_OK) return st;
-  }
-  if (d_status && n > 0) return from_cuda(cudaMemsetAsync(d_status, 0, sizeof(int) * n, s));
-  return DWT_OK;
+  std::sort(plans.begin(), plans.end());
+  for (int i = 1; i < n; ++i)
+    if (plans[i] == plans[i - 1]) return DWT_EBUSY;
+  if (n == 0) return DWT_OK;
+  // every plan of the call stays locked until the launch is queued; taking
+  // the locks in address order keeps concurrent batches from deadlocking
+  std::vector<std::unique_lock<std::mutex>> locks;
+  locks.reserve(n);
+  for (dwt_plan_s* p : plans) locks.emplace_back(p->mu);
+  return batch_submit(reqs, n, reinterpret_cast<cudaStream_t>(stream), d_status);
 }
 
 dwt_status dwt_plan_device_status(dwt_plan p) {

@@ -132,9 +132,10 @@ struct Strip {
   int lane, m0, mfirst, yfirst;
   unsigned char* sm;
   uint64_t* bars;
+  int stride = C::STAGE_BYTES;  // bytes between ring stages
 
   __device__ __forceinline__ ST* plane(int s, int p) const {
-    return reinterpret_cast<ST*>(sm + (size_t)s * C::STAGE_BYTES + p * C::PLANE_BYTES);
+    return reinterpret_cast<ST*>(sm + (size_t)s * stride + p * C::PLANE_BYTES);
   }
   __device__ __forceinline__ const ST* src_plane(int p) const {
     return static_cast<const ST*>(a.src[p]);
@@ -520,43 +521,34 @@ __device__ __forceinline__ void strip_coords(int s, int ncs, int nrs, int& cs, i
   }
 }
 
+// Lift one strip.  `ring` is the warp's shared-memory ring (nstages stages of
+// C::STAGE_BYTES, whatever stage size the caller reserved is passed as
+// `stage_stride`), `bars` its barriers (initialised for 32 arrivals), and
+// `chunk_ctr` the warp's running count of ring fills: stage and phase of a
+// fill follow from it, so a warp can lift several strips in a row.
+// Returns false if a bounded wait ran out (the launch's status word is set).
 template <class C>
-__global__ void __launch_bounds__(kWarpsPerCta * 32, C::MIN_WARPS / kWarpsPerCta)
-    level_kernel(const __grid_constant__ TmaMaps maps, const __grid_constant__ LevelArgs a,
-                 const __grid_constant__ Coefs cf, const __grid_constant__ ConvTaps ct) {
-  extern __shared__ __align__(128) unsigned char smem_raw[];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int strip = blockIdx.x * kWarpsPerCta + warp;
-  if (strip >= a.ncs * a.nrs) return;  // whole warp: no CTA-wide synchronisation is used
+__device__ __forceinline__ bool run_strip(const LevelArgs& a, const TmaMaps& maps, const Coefs& cf,
+                                          const ConvTaps& ct, int strip, unsigned char* ring,
+                                          int stage_stride, uint64_t* bars, uint32_t& chunk_ctr) {
+  const int lane = threadIdx.x & 31;
   int cs, rs;
   strip_coords(strip, a.ncs, a.nrs, cs, rs);
   const int q0 = rs * a.T;
   const int rows_out = min(a.T, a.ch - q0);
-  if (rows_out <= 0) return;
+  if (rows_out <= 0) return true;
   const int NS = a.nstages;
-
   using Tot = typename C::Tot;
-  Strip<C> sp{a, maps, lane, cs * C::UQ, cs * C::UQ - C::HQ, q0 - Tot::UP,
-              smem_raw + (size_t)warp * NS * C::STAGE_BYTES,
-              reinterpret_cast<uint64_t*>(smem_raw + (size_t)kWarpsPerCta * NS * C::STAGE_BYTES) +
-                  warp * kMaxStages};
-  ptx::launch_dependents();
-  if (lane == 0) {
-    for (int s = 0; s < NS; ++s) ptx::mbar_init(&sp.bars[s], 32);
-    ptx::fence_barrier_init();
-    if (a.src_tma) ptx::prefetch_tensormap(&maps.m[0]);
-  }
-  __syncwarp();
-  // the previous level's kernel may still be running: every read and write
-  // of level data comes after this point
-  ptx::wait_prerequisites();
+  Strip<C> sp{a, maps, lane, cs * C::UQ, cs * C::UQ - C::HQ, q0 - Tot::UP, ring, bars};
+  sp.stride = stage_stride;
 
   // rows streamed: the strip plus its halo, padded to whole chunks (the
   // extra rows are mirrored image rows, lifted but never stored)
   const int nrows = rows_out + Tot::UP + Tot::DOWN;
   const int nchunks = (nrows + C::CH - 1) / C::CH;
   const int q_end = q0 + rows_out;
-  for (int c = 0; c < NS - 1 && c < nchunks; ++c) sp.fill(c, c);
+  const uint32_t g0 = chunk_ctr;
+  for (int c = 0; c < NS - 1 && c < nchunks; ++c) sp.fill(c, (g0 + c) % NS);
 
   const typename Strip<C>::Out ob = sp.out_bases();
   const typename Strip<C>::Remap remap = sp.remap_cols();
@@ -566,18 +558,20 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, C::MIN_WARPS / kWarpsPerCta
     const int cn = c + NS - 1;
     if (cn < nchunks) {
       __syncwarp();
-      sp.fill(cn, cn % NS);
+      sp.fill(cn, (g0 + cn) % NS);
     }
-    const int s = c % NS;
-    bool ok = ptx::mbar_wait_bounded(&sp.bars[s], (c / NS) & 1, kWaitProbes);
+    const uint32_t g = g0 + c;
+    const int s = g % NS;
+    bool ok = ptx::mbar_wait_bounded(&bars[s], (g / NS) & 1, kWaitProbes);
     ok = __all_sync(kFull, ok);
     if (!ok) {
       if (lane == 0) atomicOr(a.status, 1);
       // let copies already in flight land before the warp leaves
       ptx::cp_async_wait_all();
       for (int k = c; k < nchunks && k < c + NS; ++k)
-        ptx::mbar_wait_bounded(&sp.bars[k % NS], (k / NS) & 1, kWaitProbes);
-      return;
+        ptx::mbar_wait_bounded(&bars[(g0 + k) % NS], ((g0 + k) / NS) & 1, kWaitProbes);
+      chunk_ctr = g0 + nchunks;
+      return false;
     }
     const int qc = sp.yfirst + c * C::CH - Tot::DOWN;
     // two rows per unrolled body: the stage windows rotate with period two,
@@ -590,6 +584,34 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, C::MIN_WARPS / kWarpsPerCta
       if (q >= q0 && q < q_end) sp.store_row(ob, out, q);
     }
   }
+  chunk_ctr = g0 + nchunks;
+  return true;
+}
+
+template <class C>
+__global__ void __launch_bounds__(kWarpsPerCta * 32, C::MIN_WARPS / kWarpsPerCta)
+    level_kernel(const __grid_constant__ TmaMaps maps, const __grid_constant__ LevelArgs a,
+                 const __grid_constant__ Coefs cf, const __grid_constant__ ConvTaps ct) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int strip = blockIdx.x * kWarpsPerCta + warp;
+  if (strip >= a.ncs * a.nrs) return;  // whole warp: no CTA-wide synchronisation is used
+  const int NS = a.nstages;
+  unsigned char* ring = smem_raw + (size_t)warp * NS * C::STAGE_BYTES;
+  uint64_t* bars =
+      reinterpret_cast<uint64_t*>(smem_raw + (size_t)kWarpsPerCta * NS * C::STAGE_BYTES) + warp * kMaxStages;
+  ptx::launch_dependents();
+  if (lane == 0) {
+    for (int s = 0; s < NS; ++s) ptx::mbar_init(&bars[s], 32);
+    ptx::fence_barrier_init();
+    if (a.src_tma) ptx::prefetch_tensormap(&maps.m[0]);
+  }
+  __syncwarp();
+  // the previous level's kernel may still be running: every read and write
+  // of level data comes after this point
+  ptx::wait_prerequisites();
+  uint32_t chunk_ctr = 0;
+  run_strip<C>(a, maps, cf, ct, strip, ring, C::STAGE_BYTES, bars, chunk_ctr);
 }
 
 // Per-instantiation host glue.

@@ -238,6 +238,10 @@ class Plan:
         dwt2_inverse_host(self.handle, c.data_ptr(), _pitch(c), out.data_ptr(), _pitch(out), stream)
         return out
 
+    def request(self, src, dst, inverse: bool = False) -> DwtRequest:
+        """One entry of a batch (see :func:`submit`)."""
+        return DwtRequest(self.handle, src.data_ptr(), _pitch(src), dst.data_ptr(), _pitch(dst), int(inverse))
+
     def close(self):
         if self.handle:
             dwt_plan_destroy(self.handle)
@@ -248,3 +252,12 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+def submit(requests: Sequence[DwtRequest], status=None, stream: int = 0) -> None:
+    """Run many transforms in one launch (dwt_batch_submit).  ``requests``
+    come from :meth:`Plan.request`; ``status``, if given, is a device int32
+    tensor with one slot per request."""
+    if status is not None and (status.numel() < len(requests) or status.dtype.itemsize != 4):
+        raise ValueError("status needs one int32 slot per request")
+    dwt_batch_submit(list(requests), stream, status.data_ptr() if status is not None else 0)
