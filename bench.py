@@ -13,6 +13,17 @@ bounded sample of the same workload (a 1024^2 image per step).
 
 Multi-GPU: the transform of one image does not shard, so N GPUs run N
 independent replicas (weak scaling); value = pixels of all ranks / max time.
+
+Other workloads (one JSON line each, not the headline):
+  --mode sweep    every scheme on square float32 images 1024^2..16384^2,
+                  CDF 5/3 and 9/7, 1 and 6 levels, forward and inverse
+  --mode batch    256 images of uneven sizes (3 levels, half 9/7 float32,
+                  half reversible 5/3 int32) in one persistent launch, with
+                  a strip-height autotuner, against one launch per image,
+                  plus the float16-storage 9/7 variant with its error
+  --mode serving  Poisson request stream served with continuous batching,
+                  p50/p99 latency and Gpixel/s, against one launch per
+                  request
 """
 from __future__ import annotations
 
@@ -45,6 +56,18 @@ def parse():
     ap.add_argument("--scheme", default="monolithic*")
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--mode", choices=["transform", "sweep", "batch", "serving"], default="transform")
+    ap.add_argument("--sizes", default="1024,2048,4096,8192,16384", help="sweep: square sizes")
+    ap.add_argument("--schemes", default="all", help="sweep: comma-separated scheme names")
+    ap.add_argument("--reps", type=int, default=10, help="sweep: timed repetitions per config")
+    ap.add_argument("--out", default=None, help="sweep/batch/serving: also write a markdown table here")
+    ap.add_argument("--batch-n", type=int, default=256)
+    ap.add_argument("--batch-lo", type=int, default=256)
+    ap.add_argument("--batch-hi", type=int, default=4096)
+    ap.add_argument("--batch-levels", type=int, default=3)
+    ap.add_argument("--rate", type=float, default=2000.0, help="serving: mean arrivals per second")
+    ap.add_argument("--seconds", type=float, default=20.0, help="serving: length of the arrival stream")
+    ap.add_argument("--saturate", type=int, default=2000, help="serving: requests in the saturation run")
     return ap.parse_args()
 
 
@@ -162,8 +185,284 @@ def run_reference(a, rank, world):
     }), flush=True)
 
 
+# ---------------------------------------------------------------------------
+# Other workloads
+# ---------------------------------------------------------------------------
+ALL_SCHEMES = ["rowcol", "sweldens", "iwahashi", "iwahashi*", "explosive", "explosive*", "monolithic",
+               "monolithic*", "polyphase", "polyphase*", "convolution"]
+
+
+def level_sizes(w, h, levels):
+    out = []
+    for _ in range(levels):
+        out.append((w, h))
+        w, h = (w + 1) // 2, (h + 1) // 2
+    return out
+
+
+def algorithmic_bytes(w, h, levels, es=4):
+    """Each level reads and writes its W_k x H_k plane once."""
+    return sum(2 * es * a * b for a, b in level_sizes(w, h, levels))
+
+
+class L2Flush:
+    """Writes a buffer twice the L2 size between timed repetitions."""
+
+    def __init__(self, torch):
+        props = torch.cuda.get_device_properties(torch.cuda.current_device())
+        self.l2 = getattr(props, "L2_cache_size", 128 << 20) or (128 << 20)
+        self.buf = torch.empty(2 * self.l2 // 4 + 1024, dtype=torch.float32, device="cuda")
+
+    def __call__(self):
+        self.buf.fill_(1.0)
+
+
+def time_calls(torch, fn, reps, flush=None, warm=2):
+    for _ in range(warm):
+        fn()
+    ts = []
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    for _ in range(reps):
+        if flush:
+            flush()
+        e0.record()
+        fn()
+        e1.record()
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1) * 1e3)  # us
+    return statistics.median(ts)
+
+
+def run_sweep(a):
+    import torch
+
+    from paper_1605_00561_gb300 import dwt, inputs
+    peak = float(measured_peaks()[0].get("hbm_gbs", 6800.0))
+    schemes = ALL_SCHEMES if a.schemes == "all" else a.schemes.split(",")
+    sizes = [int(x) for x in a.sizes.split(",")]
+    flush = L2Flush(torch)
+    l2 = flush.l2
+    rows = []
+    for si, n in enumerate(sizes):
+        x = torch.from_numpy(inputs.textured_image(n, n, seed=2 + si)).cuda()
+        c = torch.empty_like(x)
+        y = torch.empty_like(x)
+        resident = 2 * n * n * 4 <= l2
+        for wl in ("cdf53", "cdf97"):
+            for L in (1, 6):
+                for sc in schemes:
+                    plan = dwt.Plan(n, n, wl, L, "f32", scheme=sc)
+                    fl = flush if resident else None
+                    t_f = time_calls(torch, lambda: plan.forward(x, c), a.reps, fl)
+                    t_i = time_calls(torch, lambda: plan.inverse(c, y), a.reps, fl)
+                    torch.cuda.synchronize()
+                    assert dwt.dwt_plan_device_status(plan.handle) == dwt.DWT_OK
+                    plan.close()
+                    ab = algorithmic_bytes(n, n, L)
+                    for d, t in (("fwd", t_f), ("inv", t_i)):
+                        rows.append({"size": n, "wavelet": wl, "levels": L, "dir": d, "scheme": sc, "us": t,
+                                     "gpx_s": n * n / t / 1e3, "hbm_frac": ab / (t * 1e-6) / 1e9 / peak,
+                                     "l2": "flushed" if resident else "larger than L2"})
+        del x, c, y
+        torch.cuda.empty_cache()
+    best = {}
+    for r in rows:
+        k = (r["size"], r["wavelet"], r["levels"], r["dir"])
+        if k not in best or r["us"] < best[k]["us"]:
+            best[k] = r
+    if a.out:
+        with open(a.out, "w") as f:
+            f.write("| size | wavelet | L | dir | " + " | ".join(schemes) + " | best |\n")
+            f.write("|---" * (5 + len(schemes)) + "|\n")
+            for k in sorted(best):
+                cells = []
+                for sc in schemes:
+                    r = next(r for r in rows if (r["size"], r["wavelet"], r["levels"], r["dir"], r["scheme"]) == k + (sc,))
+                    cells.append(f"{r['us']:.1f} us / {r['hbm_frac']:.2f}")
+                f.write(f"| {k[0]} | {k[1]} | {k[2]} | {k[3]} | " + " | ".join(cells) + f" | {best[k]['scheme']} |\n")
+    print(json.dumps({"mode": "sweep", "unit": "us per transform; hbm_frac of measured copy bandwidth",
+                      "peak_gbs": peak, "rows": rows,
+                      "best": {f"{k[0]}/{k[1]}/L{k[2]}/{k[3]}": v["scheme"] for k, v in sorted(best.items())}}),
+          flush=True)
+
+
+def run_batch(a):
+    import numpy as np
+    import torch
+
+    import oracle
+    from paper_1605_00561_gb300 import dwt, inputs
+    peak = float(measured_peaks()[0].get("hbm_gbs", 6800.0))
+    L = a.batch_levels
+    shapes = inputs.batch_shapes(n=a.batch_n, seed=8, lo=a.batch_lo, hi=a.batch_hi)
+    g = torch.Generator(device="cuda")
+    g.manual_seed(8)
+    imgs, plans = [], []
+    for (w, h, kind) in shapes:
+        if kind == "cdf97":
+            x = torch.randint(0, 256, (h, w), generator=g, device="cuda", dtype=torch.int32).float()
+            plans.append(dwt.Plan(w, h, "cdf97", L, "f32"))
+        else:
+            x = torch.randint(0, 4096, (h, w), generator=g, device="cuda", dtype=torch.int32)
+            plans.append(dwt.Plan(w, h, "cdf53", L, "i32"))
+        imgs.append(x)
+    coefs = [torch.empty_like(x) for x in imgs]
+    back = [torch.empty_like(x) for x in imgs]
+    pixels = sum(w * h for w, h, _ in shapes)
+    ab = sum(algorithmic_bytes(w, h, L) for w, h, _ in shapes)
+    fwd = [p.request(x, c) for p, x, c in zip(plans, imgs, coefs)]
+    inv = [p.request(c, y, True) for p, c, y in zip(plans, coefs, back)]
+    status = torch.zeros(len(shapes), dtype=torch.int32, device="cuda")
+
+    def batch_fwd():
+        dwt.submit(fwd, status=status)
+
+    # strip-height autotuner: coordinate descent over three area classes,
+    # timing the whole batch for each candidate
+    areas = sorted(w * h for w, h, _ in shapes)
+    cuts = [areas[len(areas) // 3], areas[2 * len(areas) // 3]]
+    cls = [0 if w * h <= cuts[0] else 1 if w * h <= cuts[1] else 2 for w, h, _ in shapes]
+    choice = [10, 10, 10]
+    cands = [6, 10, 16, 24, 32, 48, 64]
+    stages = 2
+
+    def apply(ch, ns):
+        for p, c in zip(plans, cls):
+            dwt.dwt_plan_set_tile(p.handle, ch[c], ns)
+        fwd[:] = [p.request(x, c) for p, x, c in zip(plans, imgs, coefs)]
+
+    tune_log = []
+    for ns in (2, 3, 4):  # ring depth first, at the default strip height
+        apply(choice, ns)
+        t = time_calls(torch, batch_fwd, 3, warm=1)
+        tune_log.append({"stages": ns, "strip_rows": list(choice), "us": t})
+        if ns == 2 or t < best_ns_t:
+            best_ns_t, stages = t, ns
+    for k in range(3):
+        best_t, best_v = None, choice[k]
+        for v in cands:
+            trial = list(choice)
+            trial[k] = v
+            apply(trial, stages)
+            t = time_calls(torch, batch_fwd, 3, warm=1)
+            tune_log.append({"class": k, "strip_rows": v, "stages": stages, "us": t})
+            if best_t is None or t < best_t:
+                best_t, best_v = t, v
+        choice[k] = best_v
+    apply(choice, stages)
+    inv[:] = [p.request(c, y, True) for p, c, y in zip(plans, coefs, back)]
+
+    t_fwd = time_calls(torch, batch_fwd, a.steps, warm=a.warmup)
+    t_inv = time_calls(torch, lambda: dwt.submit(inv, status=status), a.steps, warm=a.warmup)
+    torch.cuda.synchronize()
+    ok_status = int(status.abs().sum()) == 0
+    exact = all(torch.equal(x, y) for x, y in zip(imgs[len(imgs) // 2:], back[len(back) // 2:]))
+
+    # one launch per image (a batch of one each), and per-level launches per
+    # image through each plan (its own scheme, default tile)
+    singles = [[r] for r in fwd]
+    t_single = time_calls(torch, lambda: [dwt.submit(r) for r in singles], max(3, a.steps // 4), warm=2)
+    for p in plans:
+        dwt.dwt_plan_set_tile(p.handle, 0, 0)
+    t_plans = time_calls(torch, lambda: [p.forward(x, c) for p, x, c in zip(plans, imgs, coefs)],
+                         max(3, a.steps // 4), warm=2)
+    torch.cuda.synchronize()
+
+    # float16 storage variant of the 9/7 half, error against FP64 on a sample
+    half = [(i, s) for i, s in enumerate(shapes) if s[2] == "cdf97"]
+    h_in = [imgs[i].half() for i, _ in half]
+    h_out = [torch.empty_like(x) for x in h_in]
+    h_plans = [dwt.Plan(w, h, "cdf97", L, "f16s") for _, (w, h, _) in half]
+    h_req = [p.request(x, o) for p, x, o in zip(h_plans, h_in, h_out)]
+    t_f16 = time_calls(torch, lambda: dwt.submit(h_req), max(3, a.steps // 2), warm=2)
+    torch.cuda.synchronize()
+    errs, errs32 = [], []
+    for j in range(0, len(half), max(1, len(half) // 4))[:4]:
+        i = half[j][0]
+        ref = oracle.dwt2(imgs[i].cpu().numpy().astype(np.float64), oracle.CDF97, L)
+        errs.append(float(np.abs(h_out[j].float().cpu().numpy() - ref).max()))
+        errs32.append(float(np.abs(coefs[i].cpu().numpy() - ref).max()))
+    f16_px = sum(w * h for _, (w, h, _) in half)
+    res = {
+        "mode": "batch", "images": len(shapes), "levels": L, "pixels": pixels,
+        "workload": f"{len(shapes)} images, w,h uniform in [{a.batch_lo}, {a.batch_hi}], {L} levels, "
+                    "half CDF 9/7 float32, half reversible 5/3 int32",
+        "batch_fwd_us": t_fwd, "batch_inv_us": t_inv,
+        "batch_fwd_gpx_s": pixels / t_fwd / 1e3, "batch_inv_gpx_s": pixels / t_inv / 1e3,
+        "batch_fwd_hbm_frac": ab / (t_fwd * 1e-6) / 1e9 / peak, "peak_gbs": peak,
+        "one_launch_per_image_us": t_single, "per_level_launches_us": t_plans,
+        "speedup_vs_one_launch_per_image": t_single / t_fwd, "speedup_vs_per_level": t_plans / t_fwd,
+        "autotuned_tile": {"class_area_cuts": cuts, "strip_rows": choice, "stages": stages, "log": tune_log},
+        "status_ok": ok_status, "int_round_trip_exact": exact,
+        "f16s_97_fwd_us": t_f16, "f16s_97_gpx_s": f16_px / t_f16 / 1e3,
+        "f16s_97_max_abs_err_vs_fp64": max(errs), "f32_97_max_abs_err_vs_fp64": max(errs32),
+        "error_sample": f"{len(errs)} of the {len(half)} 9/7 images",
+    }
+    print(json.dumps(res), flush=True)
+    for p in plans + h_plans:
+        p.close()
+
+
+def run_serving(a):
+    import torch
+
+    from paper_1605_00561_gb300 import dwt, inputs, serving
+    n = 8192
+    g = torch.Generator(device="cuda")
+    g.manual_seed(9)
+    pool_f = torch.randint(0, 256, (n, n), generator=g, device="cuda", dtype=torch.int32).float()
+    pool_i = torch.randint(0, 4096, (n, n), generator=g, device="cuda", dtype=torch.int32)
+
+    def build(trace):
+        reqs = []
+        for t in trace:
+            f = t["kind"] == "cdf97"
+            src = (pool_f if f else pool_i)[: t["h"], : t["w"]]
+            reqs.append(serving.Request(t["w"], t["h"], t["levels"], "cdf97" if f else "cdf53",
+                                        "f32" if f else "i32", False, src))
+        return reqs
+
+    trace = inputs.serving_trace(rate=a.rate, seconds=a.seconds, seed=9)
+    out = {"mode": "serving", "rate_req_s": a.rate, "seconds": a.seconds, "requests": len(trace),
+           "workload": "Poisson arrivals, area log-normal (median 1 MP, sigma 1), aspect U(0.5, 2), "
+                       "sides clipped to [64, 8192], levels U{1..6}, 70% CDF 9/7 float32 / 30% int 5/3; "
+                       "inputs are views of a device-resident pool (no host copies)"}
+    def release(r):
+        r.out = None  # the client takes its result; nothing keeps it here
+
+    def server(per):
+        return serving.Server(per_request=per, on_done=release)
+
+    # warm-up: plans, pools, kernels
+    warm = build(trace[:200])
+    for per in (False, True):
+        srv = server(per)
+        serving.replay(srv, warm, [0.0] * len(warm))
+        srv.close()
+    for name, per in (("batched", False), ("one_launch_per_request", True)):
+        srv = server(per)
+        res = serving.replay(srv, build(trace), [t["t"] for t in trace])
+        out[name] = res.summary()
+        srv.close()
+        torch.cuda.empty_cache()
+    sat = trace[: a.saturate]
+    for name, per in (("batched", False), ("one_launch_per_request", True)):
+        srv = server(per)
+        res = serving.replay(srv, build(sat), [0.0] * len(sat))
+        out[name + "_saturated"] = res.summary()
+        srv.close()
+        torch.cuda.empty_cache()
+    print(json.dumps(out), flush=True)
+
+
 def main():
     a = parse()
+    if a.mode != "transform":
+        import torch
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        {"sweep": run_sweep, "batch": run_batch, "serving": run_serving}[a.mode](a)
+        return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))

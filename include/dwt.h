@@ -54,7 +54,7 @@ typedef enum {
   DWT_EUNSUPPORTED = 3, /* valid but not provided (e.g. 9/7 with int32) */
   DWT_ECUDA = 4,        /* a CUDA runtime call failed */
   DWT_ETIMEOUT = 5,     /* a bounded device-side wait gave up */
-  DWT_EBUSY = 6         /* a resource is in use (e.g. one plan twice in a batch) */
+  DWT_EBUSY = 6         /* a resource is in use (reserved: no call of this version returns it) */
 } dwt_status;
 
 typedef enum {
@@ -87,8 +87,10 @@ typedef enum {
 typedef enum { DWT_NORM_JPEG2000 = 0, DWT_NORM_ZETA = 1 } dwt_norm;
 
 /* Create a plan for a w x h image, `levels` levels (0 = plain copy), wavelet
- * and storage type.  Allocates the plan's device scratch (about w*h/4
- * elements for the LL ping-pong).  Errors: DWT_EINVAL for w < 1, h < 1,
+ * and storage type.  Host-only: the plan's device memory (its status word
+ * and the LL ping-pong scratch, about 3/8 w*h elements) is allocated by its
+ * first single-image call, so plans used only in batches never touch
+ * device memory and are cheap to create and destroy.  Errors: DWT_EINVAL for w < 1, h < 1,
  * levels < 0, levels above the number of halvings until both dimensions
  * are 1, or out == NULL; DWT_EUNSUPPORTED for DWT_I32 with a wavelet other
  * than 5/3; DWT_ENOMEM; DWT_ECUDA. */
@@ -170,14 +172,17 @@ dwt_status dwt2_inverse_host(dwt_plan plan, const void* h_coef, size_t coef_pitc
  * the same image is done.  The scheme is fixed per dtype whatever the plan
  * selects: Monolithic* (Sec. 4) for float32 and float16 storage, the
  * separable JPEG 2000 lifting order for reversible int32 5/3; the plans'
- * normalisation and strip height apply.  d_status (device memory, n ints,
+ * normalisation and strip height apply.  Each request's LL scratch and the
+ * work list live in one work area that the call takes from a
+ * library-owned stream-ordered memory pool and returns at the end of the
+ * launch (the pool keeps its peak size for later batches), so batches
+ * leave the plans' own scratch alone.  d_status (device memory, n ints,
  * may be NULL) is cleared and then receives DWT_ETIMEOUT for any request
- * whose wait or copy gave up.  A plan may appear at most once per call
- * (DWT_EBUSY otherwise); outputs may not overlap each other or any input
- * (DWT_EINVAL).  The call uploads its work list from page-locked memory
- * and allocates its device work area stream-ordered; it synchronises with
- * the previous batch's upload on the same device, so it cannot be captured
- * into a CUDA graph. */
+ * whose wait or copy gave up.  A plan only supplies parameters here and
+ * may appear in any number of requests; outputs may not overlap each other
+ * or any input (DWT_EINVAL).  The call uploads its work list from a ring
+ * of page-locked buffers and may wait for the upload of the batch that last
+ * used its slot, so it cannot be captured into a CUDA graph. */
 typedef struct {
   dwt_plan plan;
   const void* in;

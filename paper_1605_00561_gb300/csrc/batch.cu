@@ -50,9 +50,9 @@ __constant__ ConvTaps kNoTaps;  // none of the batch kinds reads taps
 // One strip of one level.  Not inlined: each kind gets its own register
 // allocation instead of the union of all ten.
 template <class C>
-__device__ __noinline__ bool go(const BatchLevel& L, int strip, unsigned char* ring, uint64_t* bars,
-                                uint32_t& ctr) {
-  if (L.a.src_tma) {
+__device__ __noinline__ bool go(const BatchLevel& L, int strip, bool new_level, unsigned char* ring,
+                                uint64_t* bars, uint32_t& ctr) {
+  if (new_level && L.a.src_tma) {
     // the maps were uploaded by a copy, and an earlier batch may have left
     // another map at the same address in the tensor-map cache
     constexpr int nmaps = C::LOAD == SAMPLES ? 1 : 4;
@@ -61,19 +61,19 @@ __device__ __noinline__ bool go(const BatchLevel& L, int strip, unsigned char* r
   return run_strip<C>(L.a, L.maps, L.cf, kNoTaps, strip, ring, kStageStride, bars, ctr);
 }
 
-__device__ __forceinline__ bool dispatch(const BatchLevel& L, int strip, unsigned char* ring, uint64_t* bars,
-                                         uint32_t& ctr) {
+__device__ __forceinline__ bool dispatch(const BatchLevel& L, int strip, bool nl, unsigned char* ring,
+                                         uint64_t* bars, uint32_t& ctr) {
   switch (L.kind) {
-    case BK_97_F32_FWD: return go<K0>(L, strip, ring, bars, ctr);
-    case BK_97_F32_INV: return go<K1>(L, strip, ring, bars, ctr);
-    case BK_53_F32_FWD: return go<K2>(L, strip, ring, bars, ctr);
-    case BK_53_F32_INV: return go<K3>(L, strip, ring, bars, ctr);
-    case BK_53_I32_FWD: return go<K4>(L, strip, ring, bars, ctr);
-    case BK_53_I32_INV: return go<K5>(L, strip, ring, bars, ctr);
-    case BK_97_F16_FWD: return go<K6>(L, strip, ring, bars, ctr);
-    case BK_97_F16_INV: return go<K7>(L, strip, ring, bars, ctr);
-    case BK_53_F16_FWD: return go<K8>(L, strip, ring, bars, ctr);
-    case BK_53_F16_INV: return go<K9>(L, strip, ring, bars, ctr);
+    case BK_97_F32_FWD: return go<K0>(L, strip, nl, ring, bars, ctr);
+    case BK_97_F32_INV: return go<K1>(L, strip, nl, ring, bars, ctr);
+    case BK_53_F32_FWD: return go<K2>(L, strip, nl, ring, bars, ctr);
+    case BK_53_F32_INV: return go<K3>(L, strip, nl, ring, bars, ctr);
+    case BK_53_I32_FWD: return go<K4>(L, strip, nl, ring, bars, ctr);
+    case BK_53_I32_INV: return go<K5>(L, strip, nl, ring, bars, ctr);
+    case BK_97_F16_FWD: return go<K6>(L, strip, nl, ring, bars, ctr);
+    case BK_97_F16_INV: return go<K7>(L, strip, nl, ring, bars, ctr);
+    case BK_53_F16_FWD: return go<K8>(L, strip, nl, ring, bars, ctr);
+    case BK_53_F16_INV: return go<K9>(L, strip, nl, ring, bars, ctr);
   }
   return false;
 }
@@ -89,18 +89,24 @@ __device__ __forceinline__ int load_acquire(const int* p) {
 __global__ void __launch_bounds__(32, 12) batch_kernel(const __grid_constant__ BatchParams P) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + (size_t)kBatchStages * kStageStride);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + (size_t)kMaxStages * kStageStride);
   if (lane == 0) {
-    for (int s = 0; s < kBatchStages; ++s) ptx::mbar_init(&bars[s], 32);
+    for (int s = 0; s < kMaxStages; ++s) ptx::mbar_init(&bars[s], 32);
     ptx::fence_barrier_init();
   }
   __syncwarp();
   uint32_t chunk_ctr = 0;
-  for (;;) {
-    int it = 0;
-    if (lane == 0) it = atomicAdd(P.head, 1);
-    it = __shfl_sync(kFull, it, 0);
-    if (it >= P.nitems) break;
+  int fenced = -1;  // level whose tensor maps this warp has acquired
+  // the queue is popped one item ahead: the next index is fetched while the
+  // current strip streams.  A warp holding an unstarted item cannot stall
+  // the queue: the smallest unfinished item is always some warp's current
+  // one, and everything it waits for comes before it.
+  int it = 0;
+  if (lane == 0) it = atomicAdd(P.head, 1);
+  it = __shfl_sync(kFull, it, 0);
+  while (it < P.nitems) {
+    int next = 0;
+    if (lane == 0) next = atomicAdd(P.head, 1);
     const BatchItem item = P.items[it];
     const BatchLevel& L = P.levels[item.level];
     bool ok = true;
@@ -125,7 +131,8 @@ __global__ void __launch_bounds__(32, 12) batch_kernel(const __grid_constant__ B
       (void)load_acquire(&P.done[L.dep]);
       ptx::fence_proxy_async_global();
     }
-    if (ok) ok = dispatch(L, item.strip, smem_raw, bars, chunk_ctr);
+    if (ok) ok = dispatch(L, item.strip, item.level != fenced, smem_raw, bars, chunk_ctr);
+    fenced = item.level;
     if (!ok && lane == 0) atomicExch(&P.req_status[L.request], 5 /* DWT_ETIMEOUT */);
     // publish this strip: the warp's stores, then one release by lane 0
     __syncwarp();
@@ -133,9 +140,11 @@ __global__ void __launch_bounds__(32, 12) batch_kernel(const __grid_constant__ B
       __threadfence();
       atomicAdd(&P.done[item.level], 1);
     }
+    it = __shfl_sync(kFull, next, 0);
   }
 }
 
+// Geometry of a kind for the host (the kernel pointer is the batch kernel's).
 template <class C>
 void kind_info(KernelInfo* k) {
   *k = KernelInfo{};
@@ -173,7 +182,7 @@ bool batch_kind_info(int kind, KernelInfo* k) {
 }
 
 size_t batch_smem_bytes() {
-  return (size_t)kBatchStages * dev::kStageStride + (size_t)kMaxStages * 8;
+  return (size_t)kMaxStages * dev::kStageStride + (size_t)kMaxStages * 8;
 }
 
 const void* batch_kernel_fn() { return reinterpret_cast<const void*>(&dev::batch_kernel); }

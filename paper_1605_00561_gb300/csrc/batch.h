@@ -13,7 +13,6 @@ enum BatchKind : int {
   BK_97_F16_FWD, BK_97_F16_INV, BK_53_F16_FWD, BK_53_F16_INV, BK_COUNT
 };
 
-constexpr int kBatchStages = 2;
 
 // One (request, step): everything a strip of it needs.  The tensor maps come
 // first so that every element of an array of these is 64-byte aligned.

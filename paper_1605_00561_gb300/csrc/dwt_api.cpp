@@ -543,7 +543,8 @@ struct LevelIO {
 };
 
 LevelIO level_io(const dwt_plan_s* p, bool inverse, int k, const LevelArgs& a, const void* src,
-                 size_t src_pitch, const void* dst, size_t dst_pitch) {
+                 size_t src_pitch, const void* dst, size_t dst_pitch, void* const scratch[2],
+                 size_t scratch_pitch) {
   const size_t es = p->es;
   LevelIO io;
   const void* coef = inverse ? src : dst;
@@ -557,15 +558,15 @@ LevelIO level_io(const dwt_plan_s* p, bool inverse, int k, const LevelArgs& a, c
     io.band[0] = coef;
     io.bpitch[0] = (long long)(cp / es);
   } else {
-    io.band[0] = p->scratch[k & 1];
-    io.bpitch[0] = (long long)(p->scratch_pitch / es);
+    io.band[0] = scratch[k & 1];
+    io.bpitch[0] = (long long)(scratch_pitch / es);
   }
   if (k == 0) {
     io.samples = inverse ? dst : src;
     io.spitch = (long long)((inverse ? dst_pitch : src_pitch) / es);
   } else {
-    io.samples = p->scratch[(k - 1) & 1];
-    io.spitch = (long long)(p->scratch_pitch / es);
+    io.samples = scratch[(k - 1) & 1];
+    io.spitch = (long long)(scratch_pitch / es);
   }
   return io;
 }
@@ -587,6 +588,35 @@ void fused_io(const LevelIO& io, bool inverse, LevelArgs& a) {
     a.dst[0] = const_cast<void*>(io.samples);
     a.dst_pitch[0] = io.spitch;
   }
+}
+
+// A plan's own device memory (status word, LL ping-pong scratch), made on
+// its first single-image call: plans used only in batches never allocate.
+dwt_status ensure_device(dwt_plan_s* p) {
+  cudaError_t e = cudaSuccess;
+  if (!p->d_status) {
+    e = cudaMalloc(&p->d_status, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(p->d_status, 0, sizeof(int));
+    if (e != cudaSuccess) {
+      cudaFree(p->d_status);
+      p->d_status = nullptr;
+      return from_cuda(e);
+    }
+  }
+  if (p->levels >= 2 && !p->scratch[0]) {
+    p->scratch_pitch = round_up((size_t)p->W[1] * p->es, 128);
+    void *s0 = nullptr, *s1 = nullptr;
+    e = cudaMalloc(&s0, p->scratch_pitch * p->H[1]);
+    if (e == cudaSuccess) e = cudaMalloc(&s1, p->scratch_pitch * p->H[2]);
+    if (e != cudaSuccess) {
+      cudaFree(s0);
+      cudaFree(s1);
+      return from_cuda(e);
+    }
+    p->scratch[0] = s0;
+    p->scratch[1] = s1;
+  }
+  return DWT_OK;
 }
 
 // Checks shared by every call that transforms one image with a plan.
@@ -612,6 +642,8 @@ dwt_status run(dwt_plan_s* p, bool inverse, const void* src, size_t src_pitch, v
   const size_t es = p->es;
   const dwt_status chk = check_buffers(p, src, src_pitch, dst, dst_pitch);
   if (chk != DWT_OK) return chk;
+  const dwt_status dev = ensure_device(p);
+  if (dev != DWT_OK) return dev;
   p->last_stream = s;
   if (p->levels == 0)
     return from_cuda(cudaMemcpy2DAsync(dst, dst_pitch, src, src_pitch, (size_t)p->w * es, p->h,
@@ -629,7 +661,7 @@ dwt_status run(dwt_plan_s* p, bool inverse, const void* src, size_t src_pitch, v
     const int k = inverse ? Lv - 1 - step : step;
     LevelArgs a{};
     level_dims(p, k, a);
-    const LevelIO io = level_io(p, inverse, k, a, src, src_pitch, dst, dst_pitch);
+    const LevelIO io = level_io(p, inverse, k, a, src, src_pitch, dst, dst_pitch, p->scratch, p->scratch_pitch);
     const void* const* band = io.band;
     const long long* bpitch = io.bpitch;
     const void* samples = io.samples;
@@ -705,15 +737,50 @@ int batch_kind(int wavelet, int dtype, bool inverse) {
   return -1;
 }
 
-// Page-locked upload buffer for the descriptors, one per device.  A new
-// batch refills it only after the previous upload out of it completed.
-struct BatchStaging {
-  std::mutex mu;
+// Page-locked upload buffers for the work lists: a ring of slots per
+// device.  A slot is refilled only after its previous upload completed;
+// with several slots a new batch rarely waits, even when the stream of the
+// batch before it is still busy.
+constexpr int kStagingSlots = 8;
+struct StagingSlot {
   void* host = nullptr;
   size_t cap = 0;
   cudaEvent_t uploaded = nullptr;
 };
+struct BatchStaging {
+  std::mutex mu;
+  StagingSlot slot[kStagingSlots];
+  int next = 0;
+};
 BatchStaging g_staging[64];
+
+// Stream-ordered pool of the batches' work areas, one per device.  It keeps
+// the memory it has handed out (no release threshold), so a steady stream of
+// batches allocates from the driver only while its peak grows.
+cudaError_t batch_pool(int device, cudaMemPool_t* out) {
+  static std::mutex mu;
+  static cudaMemPool_t pools[64] = {};
+  std::lock_guard<std::mutex> lk(mu);
+  if (!pools[device]) {
+    cudaMemPoolProps props;
+    std::memset(&props, 0, sizeof props);
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = device;
+    cudaMemPool_t pool = nullptr;
+    cudaError_t e = cudaMemPoolCreate(&pool, &props);
+    if (e != cudaSuccess) return e;
+    uint64_t keep = UINT64_MAX;
+    e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    if (e != cudaSuccess) {
+      cudaMemPoolDestroy(pool);
+      return e;
+    }
+    pools[device] = pool;
+  }
+  *out = pools[device];
+  return cudaSuccess;
+}
 
 dwt_status batch_submit(const dwt_request* reqs, int n, cudaStream_t s, int* d_status) {
   int device = -1;
@@ -730,18 +797,28 @@ dwt_status batch_submit(const dwt_request* reqs, int n, cudaStream_t s, int* d_s
     if (kinds[i] < 0) return DWT_EUNSUPPORTED;
     maxl = std::max(maxl, p->levels);
   }
-  // images may not share memory with each other either
-  for (int i = 0; i < n; ++i)
-    for (int j = 0; j < i; ++j) {
-      const dwt_plan_s *p = reqs[i].plan, *q = reqs[j].plan;
-      const size_t ni = plane_extent(p->w, p->h, reqs[i].out_pitch, p->es);
-      const size_t nj = plane_extent(q->w, q->h, reqs[j].out_pitch, q->es);
-      const size_t ii = plane_extent(p->w, p->h, reqs[i].in_pitch, p->es);
-      const size_t ij = plane_extent(q->w, q->h, reqs[j].in_pitch, q->es);
-      if (overlaps(reqs[i].out, ni, reqs[j].out, nj) || overlaps(reqs[i].out, ni, reqs[j].in, ij) ||
-          overlaps(reqs[j].out, nj, reqs[i].in, ii))
-        return DWT_EINVAL;
+  // images may not share memory with each other either: no output range
+  // may meet another output or any input (sorted sweeps, O(n log n))
+  {
+    typedef std::pair<uintptr_t, uintptr_t> Range;  // [begin, end)
+    std::vector<Range> outs(n), ins(n);
+    for (int i = 0; i < n; ++i) {
+      const dwt_plan_s* p = reqs[i].plan;
+      const uintptr_t o = reinterpret_cast<uintptr_t>(reqs[i].out);
+      const uintptr_t x = reinterpret_cast<uintptr_t>(reqs[i].in);
+      outs[i] = Range(o, o + plane_extent(p->w, p->h, reqs[i].out_pitch, p->es));
+      ins[i] = Range(x, x + plane_extent(p->w, p->h, reqs[i].in_pitch, p->es));
     }
+    std::sort(outs.begin(), outs.end());
+    for (int i = 1; i < n; ++i)
+      if (outs[i].first < outs[i - 1].second) return DWT_EINVAL;
+    // an input meets some output iff the output starting last before the
+    // input's end reaches past the input's start (outputs are disjoint)
+    for (const Range& r : ins) {
+      auto it = std::lower_bound(outs.begin(), outs.end(), Range(r.second, 0));
+      if (it != outs.begin() && std::prev(it)->second > r.first) return DWT_EINVAL;
+    }
+  }
 
   KernelInfo kinfo[BK_COUNT];
   for (int k = 0; k < BK_COUNT; ++k)
@@ -749,10 +826,15 @@ dwt_status batch_submit(const dwt_request* reqs, int n, cudaStream_t s, int* d_s
   const Occ oc = occupancy(kinfo[0], device);
   const int resident = oc.sms * oc.per_sm;
 
-  // levels in queue order: step-major across requests, so that every strip
-  // a level waits for sits earlier in the queue
+  // ring depth: the deepest any of the plans asks for (the ring is sized
+  // for kMaxStages)
+  int nstages = 1;
+  for (int i = 0; i < n; ++i) nstages = std::max(nstages, reqs[i].plan->nstages);
+
+  // pass 1, geometry: levels in queue order, step-major across requests,
+  // so that every strip a level waits for sits earlier in the queue
   std::vector<BatchLevel> levels;
-  std::vector<int> last_of(n, -1);
+  std::vector<int> step_of, last_of(n, -1);
   size_t nitems = 0;
   for (int step = 0; step < maxl; ++step) {
     int active = 0;
@@ -768,27 +850,10 @@ dwt_status batch_submit(const dwt_request* reqs, int n, cudaStream_t s, int* d_s
       std::memset(&b, 0, sizeof b);
       LevelArgs& a = b.a;
       level_dims(p, k, a);
-      const LevelIO io = level_io(p, inverse, k, a, reqs[i].in, reqs[i].in_pitch, reqs[i].out,
-                                  reqs[i].out_pitch);
-      fused_io(io, inverse, a);
       a.ncs = (a.cw + ki.uq - 1) / ki.uq;
       a.T = strip_height(p->strip_rows, a.ch, a.ncs, cap);
       a.nrs = (a.ch + a.T - 1) / a.T;
-      a.nstages = kBatchStages;
-      a.src_tma = 0;
-      if (a.W >= 2 && a.H >= 2) {
-        if (ki.load == SAMPLES) {
-          a.src_tma = encode_2d(&b.maps.m[0], p->dtype, a.src[0], a.W, a.H,
-                                (size_t)a.src_pitch[0] * p->es, ki.box_w, ki.box_h);
-        } else {
-          const int pw[4] = {a.cw, a.fw, a.cw, a.fw}, ph[4] = {a.ch, a.ch, a.fh, a.fh};
-          bool ok = true;
-          for (int j = 0; j < 4 && ok; ++j)
-            ok = encode_2d(&b.maps.m[j], p->dtype, a.src[j], pw[j], ph[j], (size_t)a.src_pitch[j] * p->es,
-                           ki.box_w, ki.box_h);
-          a.src_tma = ok;
-        }
-      }
+      a.nstages = nstages;
       b.cf = make_coefs(lifting_of(p->wavelet), p->norm, a.W, a.H, PASS_FUSED, inverse);
       b.kind = kinds[i];
       b.request = i;
@@ -797,18 +862,32 @@ dwt_status batch_submit(const dwt_request* reqs, int n, cudaStream_t s, int* d_s
       last_of[i] = (int)levels.size();
       nitems += (size_t)b.nstrips;
       levels.push_back(b);
+      step_of.push_back(k);
     }
   }
   if (nitems > (size_t)INT32_MAX) return DWT_EINVAL;
   const int nl = (int)levels.size();
 
-  // device block: levels | items | head | done[nl] | status[n]
+  // work area: levels | items (uploaded) | LL scratch per request | head,
+  // done[nl], status[n]
   const size_t off_items = round_up(sizeof(BatchLevel) * nl, 256);
-  const size_t off_head = round_up(off_items + sizeof(BatchItem) * nitems, 256);
-  const size_t upload = off_head;
+  const size_t upload = round_up(off_items + sizeof(BatchItem) * nitems, 256);
+  std::vector<size_t> sc_off(n, 0), sc_pitch(n, 0);
+  size_t off = upload;
+  for (int i = 0; i < n; ++i) {
+    const dwt_plan_s* p = reqs[i].plan;
+    if (p->levels < 2) continue;
+    sc_pitch[i] = round_up((size_t)p->W[1] * p->es, 128);
+    sc_off[i] = off;
+    off = round_up(off + sc_pitch[i] * ((size_t)p->H[1] + p->H[2]), 256);
+  }
+  const size_t off_head = off;
   const size_t counters = sizeof(int) * (1 + (size_t)nl + (size_t)n);
-  BatchStaging& st = g_staging[device];
-  std::lock_guard<std::mutex> lk(st.mu);
+
+  BatchStaging& bs = g_staging[device];
+  std::lock_guard<std::mutex> lk(bs.mu);
+  StagingSlot& st = bs.slot[bs.next];
+  bs.next = (bs.next + 1) % kStagingSlots;
   cudaError_t e = cudaSuccess;
   if (!st.uploaded) e = cudaEventCreateWithFlags(&st.uploaded, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventSynchronize(st.uploaded);
@@ -830,9 +909,12 @@ dwt_status batch_submit(const dwt_request* reqs, int n, cudaStream_t s, int* d_s
   if (e == cudaSuccess && d_status && n) e = cudaMemsetAsync(d_status, 0, sizeof(int) * n, s);
   if (e != cudaSuccess || nitems == 0) return from_cuda(e);
 
+  cudaMemPool_t pool = nullptr;
+  e = batch_pool(device, &pool);
+  if (e != cudaSuccess) return from_cuda(e);
   // tensor maps read from global memory must be 64-byte aligned
   unsigned char* block = nullptr;
-  e = cudaMallocAsync(reinterpret_cast<void**>(&block), upload + counters + 128, s);
+  e = cudaMallocFromPoolAsync(reinterpret_cast<void**>(&block), off_head + counters + 128, pool, s);
   if (e != cudaSuccess) return from_cuda(e);
   unsigned char* d = block + ((128 - (reinterpret_cast<uintptr_t>(block) & 127)) & 127);
   int* head = reinterpret_cast<int*>(d + off_head);
@@ -840,7 +922,35 @@ dwt_status batch_submit(const dwt_request* reqs, int n, cudaStream_t s, int* d_s
   // a strip that gives up on its ring raises its level's status word: the
   // caller's slot for the request, or a slot of this block
   int* status = d_status ? d_status : done + nl;
-  for (int l = 0; l < nl; ++l) levels[l].a.status = status + levels[l].request;
+
+  // pass 2, addresses: buffers, scratch, tensor maps
+  for (int l = 0; l < nl; ++l) {
+    BatchLevel& b = levels[l];
+    const int i = b.request;
+    const dwt_plan_s* p = reqs[i].plan;
+    const bool inverse = reqs[i].inverse != 0;
+    LevelArgs& a = b.a;
+    void* const sc[2] = {d + sc_off[i], d + sc_off[i] + sc_pitch[i] * (size_t)p->H[1]};
+    const LevelIO io = level_io(p, inverse, step_of[l], a, reqs[i].in, reqs[i].in_pitch, reqs[i].out,
+                                reqs[i].out_pitch, sc, sc_pitch[i]);
+    fused_io(io, inverse, a);
+    a.status = status + i;
+    a.src_tma = 0;
+    const KernelInfo& ki = kinfo[b.kind];
+    if (a.W >= 2 && a.H >= 2) {
+      if (ki.load == SAMPLES) {
+        a.src_tma = encode_2d(&b.maps.m[0], p->dtype, a.src[0], a.W, a.H, (size_t)a.src_pitch[0] * p->es,
+                              ki.box_w, ki.box_h);
+      } else {
+        const int pw[4] = {a.cw, a.fw, a.cw, a.fw}, ph[4] = {a.ch, a.ch, a.fh, a.fh};
+        bool ok = true;
+        for (int j = 0; j < 4 && ok; ++j)
+          ok = encode_2d(&b.maps.m[j], p->dtype, a.src[j], pw[j], ph[j], (size_t)a.src_pitch[j] * p->es,
+                         ki.box_w, ki.box_h);
+        a.src_tma = ok;
+      }
+    }
+  }
   unsigned char* h = static_cast<unsigned char*>(st.host);
   std::memcpy(h, levels.data(), sizeof(BatchLevel) * nl);
   BatchItem* items = reinterpret_cast<BatchItem*>(h + off_items);
@@ -862,7 +972,6 @@ dwt_status batch_submit(const dwt_request* reqs, int n, cudaStream_t s, int* d_s
   }
   const cudaError_t ef = cudaFreeAsync(block, s);
   if (e == cudaSuccess) e = ef;
-  for (int i = 0; i < n; ++i) reqs[i].plan->last_stream = s;
   return from_cuda(e);
 }
 
@@ -1027,17 +1136,6 @@ dwt_status dwt_plan_create(int w, int h, dwt_wavelet wavelet, int levels, dwt_dt
     p->W[k] = (p->W[k - 1] + 1) / 2;
     p->H[k] = (p->H[k - 1] + 1) / 2;
   }
-  cudaError_t e = cudaMalloc(&p->d_status, sizeof(int));
-  if (e == cudaSuccess) e = cudaMemset(p->d_status, 0, sizeof(int));
-  if (e == cudaSuccess && levels >= 2) {
-    p->scratch_pitch = round_up((size_t)p->W[1] * p->es, 128);
-    e = cudaMalloc(&p->scratch[0], p->scratch_pitch * p->H[1]);
-    if (e == cudaSuccess) e = cudaMalloc(&p->scratch[1], p->scratch_pitch * p->H[2]);
-  }
-  if (e != cudaSuccess) {
-    dwt_plan_destroy(p);
-    return from_cuda(e);
-  }
   *out = p;
   return DWT_OK;
 }
@@ -1132,14 +1230,13 @@ dwt_status dwt_batch_submit(const dwt_request* reqs, int n, dwt_stream stream, i
     if (!reqs[i].plan) return DWT_EINVAL;
     plans[i] = reqs[i].plan;
   }
-  std::sort(plans.begin(), plans.end());
-  for (int i = 1; i < n; ++i)
-    if (plans[i] == plans[i - 1]) return DWT_EBUSY;
   if (n == 0) return DWT_OK;
   // every plan of the call stays locked until the launch is queued; taking
   // the locks in address order keeps concurrent batches from deadlocking
+  std::sort(plans.begin(), plans.end());
+  plans.erase(std::unique(plans.begin(), plans.end()), plans.end());
   std::vector<std::unique_lock<std::mutex>> locks;
-  locks.reserve(n);
+  locks.reserve(plans.size());
   for (dwt_plan_s* p : plans) locks.emplace_back(p->mu);
   return batch_submit(reqs, n, reinterpret_cast<cudaStream_t>(stream), d_status);
 }
@@ -1149,6 +1246,7 @@ dwt_status dwt_plan_device_status(dwt_plan p) {
   std::lock_guard<std::mutex> lk(p->mu);
   int v = 0;
   cudaError_t e = cudaStreamSynchronize(p->last_stream);
+  if (e == cudaSuccess && !p->d_status) return DWT_OK;
   if (e == cudaSuccess) e = cudaMemcpy(&v, p->d_status, sizeof v, cudaMemcpyDeviceToHost);
   if (e == cudaSuccess && v) e = cudaMemset(p->d_status, 0, sizeof(int));
   if (e != cudaSuccess) return from_cuda(e);
@@ -1245,7 +1343,10 @@ dwt_status dwt_plan_destroy(dwt_plan p) {
   if (!p) return DWT_EINVAL;
   {
     DeviceGuard g(p->device);
-    if (p->last_stream || !p->pending.empty()) cudaDeviceSynchronize();
+    // plans used only in batches own no device memory and nothing on the
+    // device refers to them: no synchronisation
+    const bool owns = p->scratch[0] || p->scratch[1] || p->tmp || p->stage_in || p->stage_out || p->d_status;
+    if (owns && (p->last_stream || !p->pending.empty())) cudaDeviceSynchronize();
     for (void* q : {p->scratch[0], p->scratch[1], p->tmp, p->stage_in, p->stage_out,
                     static_cast<void*>(p->d_status)})
       if (q) cudaFree(q);

@@ -78,9 +78,10 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
 }
 
 // Order later TMA reads of a tensor map that lives in global memory after
-// the generic-proxy writes that filled it (a map uploaded by a copy).
+// the writes that filled it.  System scope: the maps are written by the host
+// (uploaded with a copy).
 __device__ __forceinline__ void fence_tensormap_acquire(const CUtensorMap* map) {
-  asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(reinterpret_cast<uint64_t>(map))
+  asm volatile("fence.proxy.tensormap::generic.acquire.sys [%0], 128;" ::"l"(reinterpret_cast<uint64_t>(map))
                : "memory");
 }
 
