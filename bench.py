@@ -76,12 +76,25 @@ def workload_name(a):
             f"{a.levels} levels, forward + inverse, scheme {a.scheme}")
 
 
-def kernel_source_hash():
+# sources the per-level kernel of each scheme is compiled from
+LEVEL_KERNEL_SOURCES = ["dwt_internal.h", "ptx.cuh", "stages.cuh", "programs.cuh", "level_kernel.cuh",
+                        "dispatch.cuh"]
+SCHEME_SOURCE = {"rowcol": "k_rowcol.cu", "sweldens": "k_sweldens.cu", "iwahashi": "k_iwahashi.cu",
+                 "iwahashi*": "k_iwahashi.cu", "explosive": "k_explosive.cu", "explosive*": "k_explosive.cu",
+                 "monolithic": "k_monolithic.cu", "monolithic*": "k_monolithic.cu",
+                 "polyphase": "k_polyphase.cu", "polyphase*": "k_polyphase.cu", "convolution": "k_convolution.cu"}
+
+
+def kernel_source_hash(scheme="monolithic*"):
+    """Hash of the sources of one scheme's per-level kernels: DRAM traffic
+    recorded for an older version of them no longer applies."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1605_00561_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        with open(os.path.join(csrc, f), "rb") as fh:
-            h.update(f.encode() + fh.read())
+    for f in LEVEL_KERNEL_SOURCES + [SCHEME_SOURCE.get(scheme, "")]:
+        path = os.path.join(csrc, f)
+        if os.path.isfile(path):
+            with open(path, "rb") as fh:
+                h.update(f.encode() + fh.read())
     return h.hexdigest()[:16]
 
 
@@ -551,7 +564,7 @@ def main():
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
             tr = json.load(f)
         entry = tr.get(f"{a.wavelet}/{a.scheme}/{n}/L{L}/{top['name']}")
-        if entry and entry.get("kernel_hash") == kernel_source_hash():
+        if entry and entry.get("kernel_hash") == kernel_source_hash(a.scheme):
             traffic = entry["bytes_per_launch"]
     except (OSError, ValueError):
         pass

@@ -72,8 +72,8 @@ typedef enum {
 typedef enum {
   DWT_AUTO = 0,        /* chosen by the autotuner (persisted cache)                 */
   DWT_ROWCOL = 1,      /* separable, all columns then all rows through global memory */
-  DWT_SWELDENS = 2,    /* separable single-loop: T^H_P | T^V_P | S^H_U | S^V_U (Sec. 2.4) */
-  DWT_IWAHASHI = 3,    /* T^I_P | R^I_{P,U} | S^I_U (Sec. 2.5)                       */
+  DWT_SWELDENS = 2,    /* separable single-loop: T^H_P | T^V_P | S^H_U | S^V_U (Sec. 2.5) */
+  DWT_IWAHASHI = 3,    /* T^I_P | R^I_{P,U} | S^I_U (Sec. 2.6)                       */
   DWT_IWAHASHI_S = 4,  /* Iwahashi* (Sec. 4)                                        */
   DWT_EXPLOSIVE = 5,   /* T^E_P | R^E_{P,U} | S^E_U (Sec. 3.1)                      */
   DWT_EXPLOSIVE_S = 6, /* Explosive* (Sec. 4)                                       */

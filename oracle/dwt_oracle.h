@@ -16,7 +16,7 @@
  *     DD 13/7: degree-3 P and U                         (Sec. 5)
  *   - multi-level: the level is re-applied to the LL band (Sec. 1).
  *
- * Readings where the paper is silent (each is listed in the design doc):
+ * Readings where the paper is silent (readings, not statements of the paper):
  *   - whole-sample symmetric (WSS) boundary extension; a length-1 line is
  *     left untouched (no lifting, no scaling);
  *   - H samples are the odd ones and are predicted from both even

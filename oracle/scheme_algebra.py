@@ -3,7 +3,7 @@
 The paper describes every 2-D lifting scheme as a chain of 4x4 polyphase
 matrices of bivariate Laurent polynomials acting on the quadruple
 x = [LL, HL, LH, HH]^T (Sec. 2.3-2.4), separated by barriers "|".  This
-module writes those matrices down (Sec. 2.4 Sweldens, Sec. 2.5 Iwahashi,
+module writes those matrices down (Sec. 2.5 Sweldens, Sec. 2.6 Iwahashi,
 Sec. 3.1 Explosive, Sec. 3.2 Monolithic, Sec. 2.3 Polyphase, Sec. 4 the
 starred variants) so that tests can check, independently of any kernel:
 
@@ -146,7 +146,7 @@ def split0(taps: Dict[int, object]):
 # The step matrices.  p, u are 1-D tap dicts; X = horiz(x), X* = vert(x).
 # ---------------------------------------------------------------------------
 
-def T_H(p):  # Sec. 2.4, T^H_P
+def T_H(p):  # Sec. 2.5, T^H_P
     P = horiz(p)
     return with_entries({(HL, LL): P, (HH, LH): P})
 
@@ -166,7 +166,7 @@ def S_V(u):  # S^V_U
     return with_entries({(LL, LH): Us, (HL, HH): Us})
 
 
-def T_I(p):  # Sec. 2.5, T^I_P
+def T_I(p):  # Sec. 2.6, T^I_P
     P, Ps = horiz(p), vert(p)
     return with_entries({(HH, LL): P * Ps, (HH, HL): Ps, (HH, LH): P})
 

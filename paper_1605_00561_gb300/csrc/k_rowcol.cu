@@ -1,6 +1,6 @@
 // Kernels of the row-column baseline: the vertical 1-D transform and the
 // horizontal 1-D transform as two launches with the intermediate plane in
-// global memory (the separable strategy of Sec. 2.4 that the paper's
+// global memory (the separable strategy of Sec. 2.5 that the paper's
 // block-based schemes replace).  Forward: vertical (samples -> samples),
 // then horizontal (samples -> subbands).  Inverse: horizontal (subbands ->
 // samples), then vertical (samples -> samples).

@@ -11,7 +11,7 @@
 namespace dwt {
 namespace dev {
 
-// --- Sweldens (Sec. 2.4): T^H_P, T^V_P, S^H_U, S^V_U ------------------------
+// --- Sweldens (Sec. 2.5): T^H_P, T^V_P, S^H_U, S^V_U ------------------------
 template <int D, int K, int PO, int S = 1>
 using TH = Lin<D, K, false, Term<HL, LL, OP_I, PO, S>, Term<HH, LH, OP_I, PO, S>>;
 template <int D, int K, int PO, int S = 1>
@@ -21,7 +21,7 @@ using SH = Lin<D, K, false, Term<LL, HL, OP_I, UO, S>, Term<LH, HH, OP_I, UO, S>
 template <int D, int K, int UO, int S = 1>
 using SV = Lin<D, K, false, Term<LL, LH, UO, OP_I, S>, Term<HL, HH, UO, OP_I, S>>;
 
-// --- Iwahashi (Sec. 2.5): T^I_P, R^I_{P,U}, S^I_U ---------------------------
+// --- Iwahashi (Sec. 2.6): T^I_P, R^I_{P,U}, S^I_U ---------------------------
 template <int D, int K, int PO, int S = 1>
 using TI = Lin<D, K, false, Term<HH, LL, PO, PO, S>, Term<HH, HL, PO, OP_I, S>,
                Term<HH, LH, OP_I, PO, S>>;
