@@ -247,6 +247,22 @@ def time_calls(torch, fn, reps, flush=None, warm=2):
     return statistics.median(ts)
 
 
+def time_back_to_back(torch, fn, k, warm=2):
+    """Mean device time per call of k calls issued back to back (the host
+    prepares call i+1 while the GPU runs call i)."""
+    for _ in range(warm):
+        fn()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(k):
+        fn()
+    e1.record()
+    e1.synchronize()
+    return e0.elapsed_time(e1) * 1e3 / k
+
+
 def run_sweep(a):
     import torch
 
@@ -366,8 +382,17 @@ def run_batch(a):
     apply(choice, stages)
     inv[:] = [p.request(c, y, True) for p, c, y in zip(plans, coefs, back)]
 
-    t_fwd = time_calls(torch, batch_fwd, a.steps, warm=a.warmup)
-    t_inv = time_calls(torch, lambda: dwt.submit(inv, status=status), a.steps, warm=a.warmup)
+    # throughput: batches back to back; latency: one batch from the call
+    # (host planning included) to its completion
+    t_fwd = time_back_to_back(torch, batch_fwd, a.steps, warm=a.warmup)
+    t_inv = time_back_to_back(torch, lambda: dwt.submit(inv, status=status), a.steps, warm=a.warmup)
+    lat_fwd = time_calls(torch, batch_fwd, max(3, a.steps // 4), warm=1)
+    host = []
+    for _ in range(5):
+        t0 = time.perf_counter()
+        batch_fwd()
+        host.append((time.perf_counter() - t0) * 1e3)
+        torch.cuda.synchronize()
     torch.cuda.synchronize()
     ok_status = int(status.abs().sum()) == 0
     exact = all(torch.equal(x, y) for x, y in zip(imgs[len(imgs) // 2:], back[len(back) // 2:]))
@@ -375,11 +400,11 @@ def run_batch(a):
     # one launch per image (a batch of one each), and per-level launches per
     # image through each plan (its own scheme, default tile)
     singles = [[r] for r in fwd]
-    t_single = time_calls(torch, lambda: [dwt.submit(r) for r in singles], max(3, a.steps // 4), warm=2)
+    t_single = time_back_to_back(torch, lambda: [dwt.submit(r) for r in singles], max(3, a.steps // 4))
     for p in plans:
         dwt.dwt_plan_set_tile(p.handle, 0, 0)
-    t_plans = time_calls(torch, lambda: [p.forward(x, c) for p, x, c in zip(plans, imgs, coefs)],
-                         max(3, a.steps // 4), warm=2)
+    t_plans = time_back_to_back(torch, lambda: [p.forward(x, c) for p, x, c in zip(plans, imgs, coefs)],
+                                max(3, a.steps // 4))
     torch.cuda.synchronize()
 
     # float16 storage variant of the 9/7 half, error against FP64 on a sample
@@ -388,7 +413,7 @@ def run_batch(a):
     h_out = [torch.empty_like(x) for x in h_in]
     h_plans = [dwt.Plan(w, h, "cdf97", L, "f16s") for _, (w, h, _) in half]
     h_req = [p.request(x, o) for p, x, o in zip(h_plans, h_in, h_out)]
-    t_f16 = time_calls(torch, lambda: dwt.submit(h_req), max(3, a.steps // 2), warm=2)
+    t_f16 = time_back_to_back(torch, lambda: dwt.submit(h_req), max(3, a.steps // 2))
     torch.cuda.synchronize()
     errs, errs32 = [], []
     for j in range(0, len(half), max(1, len(half) // 4))[:4]:
@@ -401,7 +426,10 @@ def run_batch(a):
         "mode": "batch", "images": len(shapes), "levels": L, "pixels": pixels,
         "workload": f"{len(shapes)} images, w,h uniform in [{a.batch_lo}, {a.batch_hi}], {L} levels, "
                     "half CDF 9/7 float32, half reversible 5/3 int32",
-        "batch_fwd_us": t_fwd, "batch_inv_us": t_inv,
+        "timing": "back-to-back batches (device time per batch; host planning overlapped); "
+                  "latency = one batch from the call to completion",
+        "batch_fwd_us": t_fwd, "batch_inv_us": t_inv, "batch_fwd_latency_us": lat_fwd,
+        "host_submit_ms": statistics.median(host),
         "batch_fwd_gpx_s": pixels / t_fwd / 1e3, "batch_inv_gpx_s": pixels / t_inv / 1e3,
         "batch_fwd_hbm_frac": ab / (t_fwd * 1e-6) / 1e9 / peak, "peak_gbs": peak,
         "one_launch_per_image_us": t_single, "per_level_launches_us": t_plans,

@@ -1,18 +1,20 @@
-// The persistent batch kernel behind dwt_batch_submit: many transforms of
-// mixed sizes, level counts, wavelets, storage types and directions in one
-// launch.
+// The persistent batch kernel behind dwt_batch_submit: every level of many
+// transforms of mixed sizes, level counts, wavelets, storage types and
+// directions in one launch.
 //
-// Work items are (request, step, strip) triples, ordered step-major across
-// requests (a forward request's step j is level j; an inverse request's step
-// j is level L-1-j).  Persistent one-warp blocks pop items from a global
-// counter.  A strip of step j of a request first waits until every strip of
-// step j-1 of the same request is done (its input is that step's output);
-// items are popped in step order, so the awaited strips were all taken
-// earlier by running warps and the wait ends.  The wait is bounded: when it
-// runs out the request's status becomes DWT_ETIMEOUT and the strip is
-// skipped, never a hang.  Each kind of request runs the same strip code as
-// the per-level kernels (run_strip), with a fixed scheme: Monolithic* for
-// the float wavelets, the separable JPEG 2000 order for reversible 5/3.
+// Work items are strips of (request, level); the host orders them so that
+// every strip comes after the strips it reads (see batch_submit).
+// Persistent one-warp blocks pop items from a global counter.  Before a
+// strip of level k starts, the warp waits until the strip rows of the
+// level it reads that cover its input rows (with the halo, mirrored) are
+// complete: levels overlap as a wavefront instead of waiting for each
+// other as a whole.  Items are popped in queue order, so everything a
+// strip waits for was taken earlier by a running warp and the wait ends;
+// it is bounded all the same, and a wait that runs out sets the request's
+// status to DWT_ETIMEOUT instead of hanging.  Each kind of request runs the
+// same strip code as the per-level kernels (run_strip), with a fixed
+// scheme: Monolithic* for the float wavelets, the separable JPEG 2000
+// order for reversible 5/3.
 #include "batch.h"
 #include "dispatch.cuh"
 
@@ -20,24 +22,33 @@ namespace dwt {
 namespace dev {
 namespace {
 
-template <int WL, typename ST, bool INV>
-using FloatKind = FusedCfg<MONOLITHIC_S, WL, ST, INV>;
+template <int WL, typename ST, bool INV, bool STATIC>
+using FloatKind = FusedCfg<MONOLITHIC_S, WL, ST, INV, STATIC>;
 template <bool INV>
 using IntKind = Cfg<int, int, typename IntFused<INV>::type, INV ? SUBBANDS : SAMPLES, INV ? SAMPLES : SUBBANDS>;
 
 // The kinds a batch can hold, in BatchKind order.
-using K0 = FloatKind<W97, float, false>;
-using K1 = FloatKind<W97, float, true>;
-using K2 = FloatKind<W53, float, false>;
-using K3 = FloatKind<W53, float, true>;
+using K0 = FloatKind<W97, float, false, true>;
+using K1 = FloatKind<W97, float, true, true>;
+using K2 = FloatKind<W53, float, false, true>;
+using K3 = FloatKind<W53, float, true, true>;
 using K4 = IntKind<false>;
 using K5 = IntKind<true>;
-using K6 = FloatKind<W97, __half, false>;
-using K7 = FloatKind<W97, __half, true>;
-using K8 = FloatKind<W53, __half, false>;
-using K9 = FloatKind<W53, __half, true>;
+using K6 = FloatKind<W97, __half, false, true>;
+using K7 = FloatKind<W97, __half, true, true>;
+using K8 = FloatKind<W53, __half, false, true>;
+using K9 = FloatKind<W53, __half, true, true>;
+using R0 = FloatKind<W97, float, false, false>;
+using R1 = FloatKind<W97, float, true, false>;
+using R2 = FloatKind<W53, float, false, false>;
+using R3 = FloatKind<W53, float, true, false>;
+using R6 = FloatKind<W97, __half, false, false>;
+using R7 = FloatKind<W97, __half, true, false>;
+using R8 = FloatKind<W53, __half, false, false>;
+using R9 = FloatKind<W53, __half, true, false>;
 
 constexpr int cmax_bytes(int a, int b) { return a > b ? a : b; }
+// runtime kinds share their geometry with the static ones
 constexpr int kStageStride =
     cmax_bytes(cmax_bytes(cmax_bytes(K0::STAGE_BYTES, K1::STAGE_BYTES), cmax_bytes(K2::STAGE_BYTES, K3::STAGE_BYTES)),
                cmax_bytes(cmax_bytes(K4::STAGE_BYTES, K5::STAGE_BYTES),
@@ -50,7 +61,7 @@ __constant__ ConvTaps kNoTaps;  // none of the batch kinds reads taps
 // One strip of one level.  Not inlined: each kind gets its own register
 // allocation instead of the union of all ten.
 template <class C>
-__device__ __noinline__ bool go(const BatchLevel& L, int strip, bool new_level, unsigned char* ring,
+__device__ __noinline__ bool go(const BatchLevel& L, int cs, int rs, bool new_level, unsigned char* ring,
                                 uint64_t* bars, uint32_t& ctr) {
   if (new_level && L.a.src_tma) {
     // the maps were uploaded by a copy, and an earlier batch may have left
@@ -58,22 +69,30 @@ __device__ __noinline__ bool go(const BatchLevel& L, int strip, bool new_level, 
     constexpr int nmaps = C::LOAD == SAMPLES ? 1 : 4;
     for (int i = 0; i < nmaps; ++i) ptx::fence_tensormap_acquire(&L.maps.m[i]);
   }
-  return run_strip<C>(L.a, L.maps, L.cf, kNoTaps, strip, ring, kStageStride, bars, ctr);
+  return run_strip<C>(L.a, L.maps, L.cf, kNoTaps, cs, rs, ring, kStageStride, bars, ctr);
 }
 
-__device__ __forceinline__ bool dispatch(const BatchLevel& L, int strip, bool nl, unsigned char* ring,
+__device__ __forceinline__ bool dispatch(const BatchLevel& L, int cs, int rs, bool nl, unsigned char* ring,
                                          uint64_t* bars, uint32_t& ctr) {
   switch (L.kind) {
-    case BK_97_F32_FWD: return go<K0>(L, strip, nl, ring, bars, ctr);
-    case BK_97_F32_INV: return go<K1>(L, strip, nl, ring, bars, ctr);
-    case BK_53_F32_FWD: return go<K2>(L, strip, nl, ring, bars, ctr);
-    case BK_53_F32_INV: return go<K3>(L, strip, nl, ring, bars, ctr);
-    case BK_53_I32_FWD: return go<K4>(L, strip, nl, ring, bars, ctr);
-    case BK_53_I32_INV: return go<K5>(L, strip, nl, ring, bars, ctr);
-    case BK_97_F16_FWD: return go<K6>(L, strip, nl, ring, bars, ctr);
-    case BK_97_F16_INV: return go<K7>(L, strip, nl, ring, bars, ctr);
-    case BK_53_F16_FWD: return go<K8>(L, strip, nl, ring, bars, ctr);
-    case BK_53_F16_INV: return go<K9>(L, strip, nl, ring, bars, ctr);
+    case BK_97_F32_FWD: return go<K0>(L, cs, rs, nl, ring, bars, ctr);
+    case BK_97_F32_INV: return go<K1>(L, cs, rs, nl, ring, bars, ctr);
+    case BK_53_F32_FWD: return go<K2>(L, cs, rs, nl, ring, bars, ctr);
+    case BK_53_F32_INV: return go<K3>(L, cs, rs, nl, ring, bars, ctr);
+    case BK_53_I32_FWD: return go<K4>(L, cs, rs, nl, ring, bars, ctr);
+    case BK_53_I32_INV: return go<K5>(L, cs, rs, nl, ring, bars, ctr);
+    case BK_97_F16_FWD: return go<K6>(L, cs, rs, nl, ring, bars, ctr);
+    case BK_97_F16_INV: return go<K7>(L, cs, rs, nl, ring, bars, ctr);
+    case BK_53_F16_FWD: return go<K8>(L, cs, rs, nl, ring, bars, ctr);
+    case BK_53_F16_INV: return go<K9>(L, cs, rs, nl, ring, bars, ctr);
+    case BK_97_F32_FWD_RT: return go<R0>(L, cs, rs, nl, ring, bars, ctr);
+    case BK_97_F32_INV_RT: return go<R1>(L, cs, rs, nl, ring, bars, ctr);
+    case BK_53_F32_FWD_RT: return go<R2>(L, cs, rs, nl, ring, bars, ctr);
+    case BK_53_F32_INV_RT: return go<R3>(L, cs, rs, nl, ring, bars, ctr);
+    case BK_97_F16_FWD_RT: return go<R6>(L, cs, rs, nl, ring, bars, ctr);
+    case BK_97_F16_INV_RT: return go<R7>(L, cs, rs, nl, ring, bars, ctr);
+    case BK_53_F16_FWD_RT: return go<R8>(L, cs, rs, nl, ring, bars, ctr);
+    case BK_53_F16_INV_RT: return go<R9>(L, cs, rs, nl, ring, bars, ctr);
   }
   return false;
 }
@@ -84,8 +103,9 @@ __device__ __forceinline__ int load_acquire(const int* p) {
   return v;
 }
 
-// 12 resident one-warp blocks per SM leave 168 registers a thread, enough
-// for every kind without spills.
+// 12 resident one-warp blocks per SM leave 168 registers a thread: the
+// strip functions of the kinds (not inlined, each with its own allocation)
+// fit with at most a few bytes of spill in the rarely used ones.
 __global__ void __launch_bounds__(32, 12) batch_kernel(const __grid_constant__ BatchParams P) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31;
@@ -109,36 +129,40 @@ __global__ void __launch_bounds__(32, 12) batch_kernel(const __grid_constant__ B
     if (lane == 0) next = atomicAdd(P.head, 1);
     const BatchItem item = P.items[it];
     const BatchLevel& L = P.levels[item.level];
+    const int rs = item.strip / L.a.ncs, cs = item.strip - rs * L.a.ncs;
     bool ok = true;
-    if (L.dep >= 0) {
-      if (lane == 0) {
-        const int need = P.levels[L.dep].nstrips;
-        uint32_t spins = 0;
-        while (load_acquire(&P.done[L.dep]) < need) {
-          if (++spins > kDepSpins) {
+    if (L.dep_row_base >= 0) {
+      // lane i watches dependency row lo + i (+ 32, ...): each lane acquires
+      // the writes of the strips it watched, and the warp barrier below
+      // passes them on to the lanes that read the data
+      const int2 d = P.row_deps[L.row_base + rs];
+      const int need = L.dep_ncs;
+      for (int r0 = d.x; r0 <= d.y && ok; r0 += 32) {
+        const int r = r0 + lane;
+        bool mine = r > d.y;
+        for (uint32_t spins = 0;; ++spins) {
+          if (!mine) mine = load_acquire(&P.row_done[L.dep_row_base + r]) >= need;
+          if (__all_sync(kFull, mine)) break;
+          if (spins >= kDepSpins) {
             ok = false;
             break;
           }
-          __nanosleep(128);
+          __nanosleep(64);
         }
-        __threadfence();
       }
-      ok = __shfl_sync(kFull, ok ? 1 : 0, 0) != 0;
-      // every lane acquires the producers' writes for itself (the ping-pong
-      // LL scratch is rewritten within one launch, so no line this SM read
-      // earlier may be reused), then orders them before its TMA reads
-      // (async proxy)
-      (void)load_acquire(&P.done[L.dep]);
+      __syncwarp();
+      // the awaited strips were written through the generic proxy; this
+      // warp reads them by TMA (async proxy) as well
       ptx::fence_proxy_async_global();
     }
-    if (ok) ok = dispatch(L, item.strip, item.level != fenced, smem_raw, bars, chunk_ctr);
+    if (ok) ok = dispatch(L, cs, rs, item.level != fenced, smem_raw, bars, chunk_ctr);
     fenced = item.level;
     if (!ok && lane == 0) atomicExch(&P.req_status[L.request], 5 /* DWT_ETIMEOUT */);
     // publish this strip: the warp's stores, then one release by lane 0
     __syncwarp();
     if (lane == 0) {
       __threadfence();
-      atomicAdd(&P.done[item.level], 1);
+      atomicAdd(&P.row_done[L.row_base + rs], 1);
     }
     it = __shfl_sync(kFull, next, 0);
   }
@@ -177,6 +201,14 @@ bool batch_kind_info(int kind, KernelInfo* k) {
     case BK_97_F16_INV: kind_info<K7>(k); return true;
     case BK_53_F16_FWD: kind_info<K8>(k); return true;
     case BK_53_F16_INV: kind_info<K9>(k); return true;
+    case BK_97_F32_FWD_RT: kind_info<R0>(k); return true;
+    case BK_97_F32_INV_RT: kind_info<R1>(k); return true;
+    case BK_53_F32_FWD_RT: kind_info<R2>(k); return true;
+    case BK_53_F32_INV_RT: kind_info<R3>(k); return true;
+    case BK_97_F16_FWD_RT: kind_info<R6>(k); return true;
+    case BK_97_F16_INV_RT: kind_info<R7>(k); return true;
+    case BK_53_F16_FWD_RT: kind_info<R8>(k); return true;
+    case BK_53_F16_INV_RT: kind_info<R9>(k); return true;
   }
   return false;
 }

@@ -6,24 +6,45 @@
 
 namespace dwt {
 
-// Kinds of request a batch can hold (scheme fixed per kind: Monolithic* for
-// float, the separable JPEG 2000 order for reversible 5/3).
+// Kinds of level a batch can hold (scheme fixed per kind: Monolithic* for
+// float, the separable JPEG 2000 order for reversible 5/3).  The float kinds
+// fold their coefficients in at compile time (JPEG 2000 normalisation, both
+// axes longer than one sample); the _RT kinds read them from the
+// descriptor and serve every other level.
 enum BatchKind : int {
   BK_97_F32_FWD = 0, BK_97_F32_INV, BK_53_F32_FWD, BK_53_F32_INV, BK_53_I32_FWD, BK_53_I32_INV,
-  BK_97_F16_FWD, BK_97_F16_INV, BK_53_F16_FWD, BK_53_F16_INV, BK_COUNT
+  BK_97_F16_FWD, BK_97_F16_INV, BK_53_F16_FWD, BK_53_F16_INV,
+  BK_97_F32_FWD_RT, BK_97_F32_INV_RT, BK_53_F32_FWD_RT, BK_53_F32_INV_RT,
+  BK_97_F16_FWD_RT, BK_97_F16_INV_RT, BK_53_F16_FWD_RT, BK_53_F16_INV_RT, BK_COUNT
 };
 
+// The kind that serves a level without compile-time coefficients.
+inline int batch_runtime_kind(int kind) {
+  switch (kind) {
+    case BK_97_F32_FWD: return BK_97_F32_FWD_RT;
+    case BK_97_F32_INV: return BK_97_F32_INV_RT;
+    case BK_53_F32_FWD: return BK_53_F32_FWD_RT;
+    case BK_53_F32_INV: return BK_53_F32_INV_RT;
+    case BK_97_F16_FWD: return BK_97_F16_FWD_RT;
+    case BK_97_F16_INV: return BK_97_F16_INV_RT;
+    case BK_53_F16_FWD: return BK_53_F16_FWD_RT;
+    case BK_53_F16_INV: return BK_53_F16_INV_RT;
+    default: return kind;  // integer kinds take no float coefficients
+  }
+}
 
-// One (request, step): everything a strip of it needs.  The tensor maps come
-// first so that every element of an array of these is 64-byte aligned.
+// One (request, level): everything a strip of it needs.  The tensor maps
+// come first so that every element of an array of these is 64-byte aligned.
+// Strips are numbered row-major: strip = rs * a.ncs + cs.
 struct alignas(64) BatchLevel {
   TmaMaps maps;
   LevelArgs a;
   Coefs cf;
   int kind;
   int request;
-  int nstrips;
-  int dep;  // index of the level whose strips this one waits for, or -1
+  int row_base;      // index of this level's strip row 0 in the row arrays
+  int dep_row_base;  // the same for the level whose output it reads, or -1
+  int dep_ncs;       // column strips per row of that level
 };
 
 struct BatchItem {
@@ -34,10 +55,13 @@ struct BatchItem {
 struct BatchParams {
   const BatchLevel* levels;
   const BatchItem* items;
+  // per strip row of every level: the first and last strip rows of the
+  // level it reads that must be complete before the row may start
+  const int2* row_deps;
   int nitems;
   int* head;        // next item to take
-  int* done;        // per level: strips finished
-  int* req_status;  // per request, may be null
+  int* row_done;    // per strip row of every level: column strips finished
+  int* req_status;  // per request
 };
 
 bool batch_kind_info(int kind, KernelInfo* k);

@@ -3,6 +3,8 @@
 // for the (wavelet, dtype, direction) combinations of its group.
 #pragma once
 
+#include <type_traits>
+
 #include "level_kernel.cuh"
 
 namespace dwt {
@@ -30,29 +32,39 @@ constexpr int kQuadsPerLane =
         ? 2
         : 4;
 
-template <int SCHEME, int WL, typename ST, bool INV>
+// STATIC: coefficients folded in at compile time (StCoefs), for levels with
+// JPEG 2000 normalisation and both axes longer than one sample.
+template <int SCHEME, int WL, typename ST, bool INV, bool STATIC = false>
 using FusedCfg = Cfg<ST, float, typename FusedProgram<SCHEME, WL, INV>::type, INV ? SUBBANDS : SAMPLES,
                      INV ? SAMPLES : SUBBANDS, kQuadsPerLane<SCHEME, WL>, 8 / kQuadsPerLane<SCHEME, WL>,
-                     SCHEME == CONVOLUTION ? 8 : 16>;
+                     SCHEME == CONVOLUTION ? 8 : 16, std::conditional_t<STATIC, StCoefs<WL, INV>, RtTag>>;
 
-// The eight float combinations of one fused scheme.
-template <int SCHEME>
+template <int SCHEME, int WL, typename ST, bool STATIC>
+inline bool fused_dir(bool inv, int ns, KernelInfo* info, const LaunchCall* call, cudaError_t* err) {
+  return inv ? run<FusedCfg<SCHEME, WL, ST, true, STATIC>>(ns, info, call, err)
+             : run<FusedCfg<SCHEME, WL, ST, false, STATIC>>(ns, info, call, err);
+}
+
+// The float combinations of one fused scheme; schemes listed with
+// WITH_STATIC also carry compile-time-coefficient kernels, taken when the
+// launch allows them.
+template <int SCHEME, bool WITH_STATIC = false>
 inline bool fused_float(const LaunchKey& k, int ns, KernelInfo* info, const LaunchCall* call,
                         cudaError_t* err) {
   if (k.pass != PASS_FUSED || k.scheme != SCHEME) return false;
   const bool inv = k.inverse != 0;
-  if (k.wavelet == W53 && k.dtype == F32)
-    return inv ? run<FusedCfg<SCHEME, W53, float, true>>(ns, info, call, err)
-               : run<FusedCfg<SCHEME, W53, float, false>>(ns, info, call, err);
-  if (k.wavelet == W97 && k.dtype == F32)
-    return inv ? run<FusedCfg<SCHEME, W97, float, true>>(ns, info, call, err)
-               : run<FusedCfg<SCHEME, W97, float, false>>(ns, info, call, err);
-  if (k.wavelet == W53 && k.dtype == F16S)
-    return inv ? run<FusedCfg<SCHEME, W53, __half, true>>(ns, info, call, err)
-               : run<FusedCfg<SCHEME, W53, __half, false>>(ns, info, call, err);
-  if (k.wavelet == W97 && k.dtype == F16S)
-    return inv ? run<FusedCfg<SCHEME, W97, __half, true>>(ns, info, call, err)
-               : run<FusedCfg<SCHEME, W97, __half, false>>(ns, info, call, err);
+  if constexpr (WITH_STATIC) {
+    if (k.static_coefs) {
+      if (k.wavelet == W53 && k.dtype == F32) return fused_dir<SCHEME, W53, float, true>(inv, ns, info, call, err);
+      if (k.wavelet == W97 && k.dtype == F32) return fused_dir<SCHEME, W97, float, true>(inv, ns, info, call, err);
+      if (k.wavelet == W53 && k.dtype == F16S) return fused_dir<SCHEME, W53, __half, true>(inv, ns, info, call, err);
+      if (k.wavelet == W97 && k.dtype == F16S) return fused_dir<SCHEME, W97, __half, true>(inv, ns, info, call, err);
+    }
+  }
+  if (k.wavelet == W53 && k.dtype == F32) return fused_dir<SCHEME, W53, float, false>(inv, ns, info, call, err);
+  if (k.wavelet == W97 && k.dtype == F32) return fused_dir<SCHEME, W97, float, false>(inv, ns, info, call, err);
+  if (k.wavelet == W53 && k.dtype == F16S) return fused_dir<SCHEME, W53, __half, false>(inv, ns, info, call, err);
+  if (k.wavelet == W97 && k.dtype == F16S) return fused_dir<SCHEME, W97, __half, false>(inv, ns, info, call, err);
   return false;
 }
 

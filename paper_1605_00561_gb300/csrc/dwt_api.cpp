@@ -13,6 +13,7 @@
 #include <map>
 #include <mutex>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "batch.h"
@@ -26,13 +27,6 @@ namespace {
 // Wavelets (Sec. 5)
 // ---------------------------------------------------------------------------
 
-// CDF 9/7 lifting constants and the DC gain K of the unscaled low-pass; the
-// paper defers them to its reference [Daubechies1998] (Sec. 5).
-constexpr double kAlpha = -1.586134342059924;
-constexpr double kBeta = -0.052980118572961;
-constexpr double kGamma = 0.882911075530934;
-constexpr double kDelta = 0.443506852043971;
-constexpr double kK97 = 1.230174104914001;
 
 struct Lifting {
   int npairs;
@@ -227,27 +221,28 @@ struct Occ {
   int per_sm = 0;
 };
 std::mutex g_occ_mu;
-std::map<std::pair<const void*, int>, Occ> g_occ;
+std::map<std::tuple<const void*, int, size_t>, Occ> g_occ;
 
-Occ occupancy(const KernelInfo& ki, int device) {
+// Resident blocks of one warp for kernel `fn` with `smem` bytes of dynamic
+// shared memory per block.
+Occ occupancy(const void* fn, size_t smem, int device) {
   std::lock_guard<std::mutex> lk(g_occ_mu);
-  auto key = std::make_pair(ki.fn, device);
+  auto key = std::make_tuple(fn, device, smem);
   auto it = g_occ.find(key);
   if (it != g_occ.end()) return it->second;
   Occ o;
   cudaDeviceGetAttribute(&o.sms, cudaDevAttrMultiProcessorCount, device);
   int optin = 0;
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
-  cudaFuncSetAttribute(ki.fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       optin > 0 ? optin : (int)ki.smem_bytes);
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o.per_sm, ki.fn, kWarpsPerCta * 32,
-                                                    ki.smem_bytes) != cudaSuccess)
+  cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, optin > 0 ? optin : (int)smem);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o.per_sm, fn, kWarpsPerCta * 32, smem) != cudaSuccess)
     o.per_sm = 1;
   o.sms = std::max(o.sms, 1);
   o.per_sm = std::max(o.per_sm, 1);
   g_occ[key] = o;
   return o;
 }
+Occ occupancy(const KernelInfo& ki, int device) { return occupancy(ki.fn, ki.smem_bytes, device); }
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
                                   const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
@@ -304,6 +299,15 @@ int strip_height(int target, int ch, int ncs, int cap_warps) {
 }
 
 size_t round_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// Whole-sample symmetric extension of index i on a line of n >= 2 samples
+// (period 2(n - 1)), as the kernels apply it.
+int host_mirror(int i, int n) {
+  const int period = 2 * (n - 1);
+  i %= period;
+  if (i < 0) i += period;
+  return i >= n ? period - i : i;
+}
 
 }  // namespace
 
@@ -478,7 +482,15 @@ dwt_status launch(dwt_plan_s* p, const LaunchKey& key, LevelArgs& a, const Coefs
   a.ncs = (a.cw + ki.uq - 1) / ki.uq;
   a.T = strip_height(p->strip_rows, a.ch, a.ncs, cap);
   a.nrs = (a.ch + a.T - 1) / a.T;
+  // a level that does not fill the GPU once is latency-bound: a deeper
+  // ring lets each (short) strip issue all its chunk loads at once, as long
+  // as the level still fits one wave with the larger shared-memory ring
   a.nstages = p->nstages;
+  if (p->nstages < kMaxStages && (long long)a.ncs * a.nrs < cap) {
+    const size_t stage = (ki.smem_bytes - (size_t)kWarpsPerCta * kMaxStages * 8) / p->nstages;
+    const Occ deep = occupancy(ki.fn, stage * kMaxStages + (size_t)kWarpsPerCta * kMaxStages * 8, p->device);
+    if ((long long)a.ncs * a.nrs <= (long long)deep.sms * deep.per_sm) a.nstages = kMaxStages;
+  }
   a.status = p->d_status;
 
   TmaMaps maps;
@@ -532,9 +544,12 @@ dwt_status ensure_tmp(dwt_plan_s* p) {
 }
 
 // Where level k of a transform reads and writes (Mallat layout): the four
-// subband planes inside the coefficient buffer, with LL in the plan's
-// scratch except at the coarsest level, and the level's sample plane (the
-// image at level 0, the finer level's LL scratch above).
+// subband planes inside the coefficient buffer, with LL_k in the buffer
+// ll[k] (pitch llp[k] bytes) except at the coarsest level, and the level's
+// sample plane (the image at level 0, LL_{k-1} above).  Single-image calls
+// pass the plan's ping-pong scratch for every k; batches give each level
+// its own buffer, so that overlapping levels never overwrite data another
+// level still reads.
 struct LevelIO {
   const void* band[4];
   long long bpitch[4];
@@ -543,8 +558,7 @@ struct LevelIO {
 };
 
 LevelIO level_io(const dwt_plan_s* p, bool inverse, int k, const LevelArgs& a, const void* src,
-                 size_t src_pitch, const void* dst, size_t dst_pitch, void* const scratch[2],
-                 size_t scratch_pitch) {
+                 size_t src_pitch, const void* dst, size_t dst_pitch, void* const* ll, const size_t* llp) {
   const size_t es = p->es;
   LevelIO io;
   const void* coef = inverse ? src : dst;
@@ -558,15 +572,15 @@ LevelIO level_io(const dwt_plan_s* p, bool inverse, int k, const LevelArgs& a, c
     io.band[0] = coef;
     io.bpitch[0] = (long long)(cp / es);
   } else {
-    io.band[0] = scratch[k & 1];
-    io.bpitch[0] = (long long)(scratch_pitch / es);
+    io.band[0] = ll[k];
+    io.bpitch[0] = (long long)(llp[k] / es);
   }
   if (k == 0) {
     io.samples = inverse ? dst : src;
     io.spitch = (long long)((inverse ? dst_pitch : src_pitch) / es);
   } else {
-    io.samples = scratch[(k - 1) & 1];
-    io.spitch = (long long)(scratch_pitch / es);
+    io.samples = ll[k - 1];
+    io.spitch = (long long)(llp[k - 1] / es);
   }
   return io;
 }
@@ -657,11 +671,15 @@ dwt_status run(dwt_plan_s* p, bool inverse, const void* src, size_t src_pitch, v
   const Lifting L = lifting_of(p->wavelet);
   const int Lv = p->levels;
   char slot[32];
+  // LL ping-pong: LL_k in scratch[k & 1]
+  std::vector<void*> ll(Lv);
+  std::vector<size_t> llp(Lv, p->scratch_pitch);
+  for (int k = 0; k < Lv; ++k) ll[k] = p->scratch[k & 1];
   for (int step = 0; step < Lv; ++step) {
     const int k = inverse ? Lv - 1 - step : step;
     LevelArgs a{};
     level_dims(p, k, a);
-    const LevelIO io = level_io(p, inverse, k, a, src, src_pitch, dst, dst_pitch, p->scratch, p->scratch_pitch);
+    const LevelIO io = level_io(p, inverse, k, a, src, src_pitch, dst, dst_pitch, ll.data(), llp.data());
     const void* const* band = io.band;
     const long long* bpitch = io.bpitch;
     const void* samples = io.samples;
@@ -673,7 +691,8 @@ dwt_status run(dwt_plan_s* p, bool inverse, const void* src, size_t src_pitch, v
       return DWT_EUNSUPPORTED;
     dwt_status st;
     if (scheme != DWT_ROWCOL) {
-      LaunchKey key{p->wavelet, p->dtype, scheme, PASS_FUSED, inverse ? 1 : 0};
+      LaunchKey key{p->wavelet, p->dtype, scheme, PASS_FUSED, inverse ? 1 : 0,
+                    p->norm == DWT_NORM_JPEG2000 && a.W >= 2 && a.H >= 2 ? 1 : 0};
       fused_io(io, inverse, a);
       std::snprintf(slot, sizeof slot, "%s/L%d", inverse ? "inv" : "fwd", k);
       st = launch(p, key, a, cf, ct, s, slot);
@@ -831,21 +850,21 @@ dwt_status batch_submit(const dwt_request* reqs, int n, cudaStream_t s, int* d_s
   int nstages = 1;
   for (int i = 0; i < n; ++i) nstages = std::max(nstages, reqs[i].plan->nstages);
 
-  // pass 1, geometry: levels in queue order, step-major across requests,
-  // so that every strip a level waits for sits earlier in the queue
+  // pass 1, geometry: every (request, level) in step order per request,
+  // with its strip rows numbered consecutively
+  std::vector<int> active(maxl + 1, 0);
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < reqs[i].plan->levels; ++j) ++active[j];
   std::vector<BatchLevel> levels;
-  std::vector<int> step_of, last_of(n, -1);
-  size_t nitems = 0;
-  for (int step = 0; step < maxl; ++step) {
-    int active = 0;
-    for (int i = 0; i < n; ++i) active += reqs[i].plan->levels > step;
-    const int cap = std::max(1, resident / std::max(active, 1));
-    for (int i = 0; i < n; ++i) {
-      const dwt_plan_s* p = reqs[i].plan;
-      if (p->levels <= step) continue;
-      const bool inverse = reqs[i].inverse != 0;
+  std::vector<int> level_of(0), step_of(0);
+  int nrows = 0;
+  for (int i = 0; i < n; ++i) {
+    const dwt_plan_s* p = reqs[i].plan;
+    const bool inverse = reqs[i].inverse != 0;
+    const KernelInfo& ki = kinfo[kinds[i]];
+    for (int step = 0; step < p->levels; ++step) {
       const int k = inverse ? p->levels - 1 - step : step;
-      const KernelInfo& ki = kinfo[kinds[i]];
+      const int cap = std::max(1, resident / std::max(active[step], 1));
       BatchLevel b;
       std::memset(&b, 0, sizeof b);
       LevelArgs& a = b.a;
@@ -855,34 +874,129 @@ dwt_status batch_submit(const dwt_request* reqs, int n, cudaStream_t s, int* d_s
       a.nrs = (a.ch + a.T - 1) / a.T;
       a.nstages = nstages;
       b.cf = make_coefs(lifting_of(p->wavelet), p->norm, a.W, a.H, PASS_FUSED, inverse);
-      b.kind = kinds[i];
+      const bool static_ok = p->norm == DWT_NORM_JPEG2000 && a.W >= 2 && a.H >= 2;
+      b.kind = static_ok ? kinds[i] : batch_runtime_kind(kinds[i]);
       b.request = i;
-      b.nstrips = a.ncs * a.nrs;
-      b.dep = last_of[i];
-      last_of[i] = (int)levels.size();
-      nitems += (size_t)b.nstrips;
+      b.row_base = nrows;
+      b.dep_row_base = step > 0 ? levels.back().row_base : -1;
+      b.dep_ncs = step > 0 ? levels.back().a.ncs : 0;
+      nrows += a.nrs;
       levels.push_back(b);
-      step_of.push_back(k);
+      level_of.push_back(k);
+      step_of.push_back(step);
     }
   }
-  if (nitems > (size_t)INT32_MAX) return DWT_EINVAL;
   const int nl = (int)levels.size();
 
-  // work area: levels | items (uploaded) | LL scratch per request | head,
-  // done[nl], status[n]
+  // which strip rows of the level it reads each strip row needs: the rows
+  // its chunks load (strip plus halo, padded to whole chunks), mirrored
+  // the way the kernel mirrors them, mapped to the strip rows that write
+  // them.  In-range rows map monotonically (their span is exact); only the
+  // few halo rows beyond an edge are mirrored one by one.
+  std::vector<int2> row_deps(nrows, make_int2(0, -1));
+  for (int l = 0; l < nl; ++l) {
+    const BatchLevel& bl = levels[l];
+    if (bl.dep_row_base < 0) continue;
+    const BatchLevel& dl = levels[l - 1];
+    const KernelInfo& ki = kinfo[bl.kind];
+    const bool inverse = reqs[bl.request].inverse != 0;
+    const LevelArgs& a = bl.a;
+    const int CH = ki.load == SAMPLES ? ki.box_h / 2 : ki.box_h;
+    // forward: sample rows of the level = LL quad rows of the level before,
+    // written by its strip row y / T; inverse: LL plane rows = sample rows
+    // of the coarser level's output, written by its strip row y / (2 T)
+    const int n = inverse ? a.ch : a.H;
+    const int per = inverse ? 2 * dl.a.T : dl.a.T;
+    auto row_of = [&](int y) {
+      int ym;
+      if (inverse) ym = a.H == 1 ? 0 : (y >= 0 && y < a.ch) ? y : (host_mirror(2 * y, a.H) >> 1);
+      else ym = a.H == 1 ? 0 : host_mirror(y, a.H);
+      return ym / per;
+    };
+    for (int rs = 0; rs < a.nrs; ++rs) {
+      const int q0 = rs * a.T;
+      const int rows_out = std::min(a.T, a.ch - q0);
+      const int nchunks = (rows_out + ki.up + ki.down + CH - 1) / CH;
+      const int y0 = q0 - ki.up, y1 = y0 + nchunks * CH;  // quad rows loaded
+      const int r0 = inverse ? y0 : 2 * y0, r1 = inverse ? y1 : 2 * y1;  // rows of the read plane
+      int lo = INT32_MAX, hi = -1;
+      const int in0 = std::max(r0, 0), in1 = std::min(r1, n);
+      if (in0 < in1) {
+        lo = in0 / per;
+        hi = (in1 - 1) / per;
+      }
+      for (int y = r0; y < std::min(r1, 0); ++y) {
+        lo = std::min(lo, row_of(y));
+        hi = std::max(hi, row_of(y));
+      }
+      for (int y = std::max(r0, n); y < r1; ++y) {
+        lo = std::min(lo, row_of(y));
+        hi = std::max(hi, row_of(y));
+      }
+      row_deps[bl.row_base + rs] = make_int2(std::max(lo, 0), std::min(hi, dl.a.nrs - 1));
+    }
+  }
+
+  // queue order: a wavefront.  The first level of each request enters in
+  // request order; a strip row of a later level is placed three resident
+  // waves of items after the last row it depends on: items popped that long
+  // ago have almost always finished (a warp pops one item per strip time),
+  // so the row rarely waits, and the levels of different requests overlap.
+  // Every row comes strictly after its dependencies (keys grow by the lag),
+  // which is what keeps the persistent kernel's waits finite.
+  const long long lag = 3LL * resident;
+  struct OrderedRow {
+    long long key;
+    int step, level, rs;
+  };
+  std::vector<OrderedRow> rows(nrows);
+  {
+    long long root = 0;
+    for (int l = 0; l < nl; ++l) {
+      const BatchLevel& bl = levels[l];
+      for (int rs = 0; rs < bl.a.nrs; ++rs) {
+        long long k;
+        if (bl.dep_row_base < 0) {
+          root += bl.a.ncs;
+          k = root;
+        } else {
+          const int2 d = row_deps[bl.row_base + rs];
+          long long m = 0;
+          for (int r = d.x; r <= d.y; ++r) m = std::max(m, rows[bl.dep_row_base + r].key);
+          k = m + lag;
+        }
+        rows[bl.row_base + rs] = OrderedRow{k, step_of[l], l, rs};
+      }
+    }
+  }
+  std::sort(rows.begin(), rows.end(), [](const OrderedRow& x, const OrderedRow& y) {
+    if (x.key != y.key) return x.key < y.key;
+    if (x.step != y.step) return x.step < y.step;
+    if (x.level != y.level) return x.level < y.level;
+    return x.rs < y.rs;
+  });
+  size_t nitems = 0;
+  for (const BatchLevel& bl : levels) nitems += (size_t)bl.a.ncs * bl.a.nrs;
+  if (nitems > (size_t)INT32_MAX) return DWT_EINVAL;
+
+  // work area: levels | items | row deps (uploaded) | per-request LL
+  // buffers | head, row_done[nrows], status[n]
   const size_t off_items = round_up(sizeof(BatchLevel) * nl, 256);
-  const size_t upload = round_up(off_items + sizeof(BatchItem) * nitems, 256);
-  std::vector<size_t> sc_off(n, 0), sc_pitch(n, 0);
+  const size_t off_deps = round_up(off_items + sizeof(BatchItem) * nitems, 256);
+  const size_t upload = round_up(off_deps + sizeof(int2) * (size_t)nrows, 256);
+  std::vector<std::vector<size_t>> ll_off(n), ll_pitch(n);
   size_t off = upload;
   for (int i = 0; i < n; ++i) {
     const dwt_plan_s* p = reqs[i].plan;
-    if (p->levels < 2) continue;
-    sc_pitch[i] = round_up((size_t)p->W[1] * p->es, 128);
-    sc_off[i] = off;
-    off = round_up(off + sc_pitch[i] * ((size_t)p->H[1] + p->H[2]), 256);
+    for (int k = 0; k + 1 < p->levels; ++k) {
+      const size_t pitch = round_up((size_t)p->W[k + 1] * p->es, 128);
+      ll_off[i].push_back(off);
+      ll_pitch[i].push_back(pitch);
+      off = round_up(off + pitch * p->H[k + 1], 256);
+    }
   }
   const size_t off_head = off;
-  const size_t counters = sizeof(int) * (1 + (size_t)nl + (size_t)n);
+  const size_t counters = sizeof(int) * (1 + (size_t)nrows + (size_t)n);
 
   BatchStaging& bs = g_staging[device];
   std::lock_guard<std::mutex> lk(bs.mu);
@@ -918,21 +1032,22 @@ dwt_status batch_submit(const dwt_request* reqs, int n, cudaStream_t s, int* d_s
   if (e != cudaSuccess) return from_cuda(e);
   unsigned char* d = block + ((128 - (reinterpret_cast<uintptr_t>(block) & 127)) & 127);
   int* head = reinterpret_cast<int*>(d + off_head);
-  int* done = head + 1;
+  int* row_done = head + 1;
   // a strip that gives up on its ring raises its level's status word: the
   // caller's slot for the request, or a slot of this block
-  int* status = d_status ? d_status : done + nl;
+  int* status = d_status ? d_status : row_done + nrows;
 
-  // pass 2, addresses: buffers, scratch, tensor maps
+  // pass 2, addresses: buffers, LL buffers, tensor maps
   for (int l = 0; l < nl; ++l) {
     BatchLevel& b = levels[l];
     const int i = b.request;
     const dwt_plan_s* p = reqs[i].plan;
     const bool inverse = reqs[i].inverse != 0;
     LevelArgs& a = b.a;
-    void* const sc[2] = {d + sc_off[i], d + sc_off[i] + sc_pitch[i] * (size_t)p->H[1]};
-    const LevelIO io = level_io(p, inverse, step_of[l], a, reqs[i].in, reqs[i].in_pitch, reqs[i].out,
-                                reqs[i].out_pitch, sc, sc_pitch[i]);
+    std::vector<void*> ll(ll_off[i].size());
+    for (size_t k = 0; k < ll.size(); ++k) ll[k] = d + ll_off[i][k];
+    const LevelIO io = level_io(p, inverse, level_of[l], a, reqs[i].in, reqs[i].in_pitch, reqs[i].out,
+                                reqs[i].out_pitch, ll.data(), ll_pitch[i].data());
     fused_io(io, inverse, a);
     a.status = status + i;
     a.src_tma = 0;
@@ -955,8 +1070,11 @@ dwt_status batch_submit(const dwt_request* reqs, int n, cudaStream_t s, int* d_s
   std::memcpy(h, levels.data(), sizeof(BatchLevel) * nl);
   BatchItem* items = reinterpret_cast<BatchItem*>(h + off_items);
   size_t it = 0;
-  for (int l = 0; l < nl; ++l)
-    for (int sidx = 0; sidx < levels[l].nstrips; ++sidx) items[it++] = BatchItem{l, sidx};
+  for (const OrderedRow& r : rows) {
+    const int ncs = levels[r.level].a.ncs;
+    for (int cs = 0; cs < ncs; ++cs) items[it++] = BatchItem{r.level, r.rs * ncs + cs};
+  }
+  std::memcpy(h + off_deps, row_deps.data(), sizeof(int2) * (size_t)nrows);
   e = cudaMemcpyAsync(d, h, upload, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaEventRecord(st.uploaded, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(head, 0, counters, s);
@@ -964,9 +1082,10 @@ dwt_status batch_submit(const dwt_request* reqs, int n, cudaStream_t s, int* d_s
     BatchParams bp;
     bp.levels = reinterpret_cast<const BatchLevel*>(d);
     bp.items = reinterpret_cast<const BatchItem*>(d + off_items);
+    bp.row_deps = reinterpret_cast<const int2*>(d + off_deps);
     bp.nitems = (int)nitems;
     bp.head = head;
-    bp.done = done;
+    bp.row_done = row_done;
     bp.req_status = status;
     e = launch_batch(bp, (int)std::min<size_t>((size_t)resident, nitems), s);
   }
@@ -1052,7 +1171,7 @@ dwt_status forward_on_scratch(int w, int h, int wavelet, int levels, int dtype, 
     const Coefs cf = make_coefs(L, DWT_NORM_JPEG2000, a.W, a.H, PASS_FUSED, false);
     ConvTaps ct;
     std::memset(&ct, 0, sizeof ct);
-    const LaunchKey key{wavelet, dtype, scheme, PASS_FUSED, 0};
+    const LaunchKey key{wavelet, dtype, scheme, PASS_FUSED, 0, a.W >= 2 && a.H >= 2 ? 1 : 0};
     KernelInfo ki{};
     if (!find_kernel(key, kDefaultStages, &ki)) return DWT_EUNSUPPORTED;
     int sms = 0, per_sm = 0;
@@ -1068,7 +1187,7 @@ dwt_status forward_on_scratch(int w, int h, int wavelet, int levels, int dtype, 
     a.ncs = (a.cw + ki.uq - 1) / ki.uq;
     a.T = strip_height(kDefaultStripRows, a.ch, a.ncs, cap);
     a.nrs = (a.ch + a.T - 1) / a.T;
-    a.nstages = kDefaultStages;
+    a.nstages = (long long)a.ncs * a.nrs < cap ? kMaxStages : kDefaultStages;
     a.status = d_status;
     TmaMaps maps;
     std::memset(&maps, 0, sizeof maps);

@@ -30,6 +30,16 @@ enum Pass : int {
   PASS_HORZ = 2     // row-column baseline: horizontal 1-D transform
 };
 
+// CDF 9/7 lifting constants and the DC gain K of the unscaled low-pass; the
+// paper defers them to its reference [Daubechies1998] (Sec. 5).  Host code
+// (coefficient tables) and device code (compile-time coefficients) share
+// these literals.
+constexpr double kAlpha = -1.586134342059924;
+constexpr double kBeta = -0.052980118572961;
+constexpr double kGamma = 0.882911075530934;
+constexpr double kDelta = 0.443506852043971;
+constexpr double kK97 = 1.230174104914001;
+
 constexpr int kWarpsPerCta = 1;  // independent warps (one strip each) per CTA
 constexpr int kMaxStages = 4;    // ring depth per warp
 constexpr int kDefaultStages = 2;
@@ -92,6 +102,9 @@ struct KernelInfo {
 
 struct LaunchKey {
   int wavelet, dtype, scheme, pass, inverse;
+  // the level may use compile-time coefficients: fused pass, JPEG 2000
+  // normalisation, both axes longer than one sample
+  int static_coefs;
 };
 
 struct LaunchCall {

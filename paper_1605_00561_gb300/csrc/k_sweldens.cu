@@ -13,7 +13,7 @@ bool group_sweldens(const LaunchKey& k, int ns, KernelInfo* info, const LaunchCa
                ? dev::run<dev::Cfg<int, int, dev::IntFused<true>::type, SUBBANDS, SAMPLES>>(ns, info, call, err)
                : dev::run<dev::Cfg<int, int, dev::IntFused<false>::type, SAMPLES, SUBBANDS>>(ns, info, call, err);
   }
-  if (dev::fused_float<SWELDENS>(k, ns, info, call, err)) return true;
+  if (dev::fused_float<SWELDENS, true>(k, ns, info, call, err)) return true;
   return false;
 }
 

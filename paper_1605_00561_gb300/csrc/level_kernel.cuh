@@ -74,8 +74,9 @@ __device__ __forceinline__ void copy_bytes(void* d, const void* s) {
 }
 
 template <typename ST_, typename VT_, class PROG_, int LOAD_, int STORE_, int QL_ = 4, int CH_ = 2,
-          int MINW_ = 16>
+          int MINW_ = 16, class CSRC_ = RtTag>
 struct Cfg {
+  using CSRC = CSRC_;  // coefficient source: RtTag (from Coefs) or StCoefs<...>
   using ST = ST_;
   using VT = VT_;
   using PROG = PROG_;
@@ -133,6 +134,7 @@ struct Strip {
   unsigned char* sm;
   uint64_t* bars;
   int stride = C::STAGE_BYTES;  // bytes between ring stages
+  bool box = false;             // chunks land in the TMA box layout (see boxed())
 
   __device__ __forceinline__ ST* plane(int s, int p) const {
     return reinterpret_cast<ST*>(sm + (size_t)s * stride + p * C::PLANE_BYTES);
@@ -204,6 +206,61 @@ struct Strip {
     return rows && cols_by_tma();
   }
   // ---- fills ---------------------------------------------------------------
+  // The box a TMA load would bring, copied by the lanes with cp.async: for
+  // chunks the TMA engine cannot take (rows to mirror at the top or bottom,
+  // a plane whose base or pitch is not 16-byte aligned, as the Mallat bands
+  // of most odd sizes are).  The shared-memory layout is the TMA box's, so
+  // the consumer side is the same.  Lanes copy consecutive 16-byte groups
+  // (4-byte ones on rows that are not 16-byte aligned); columns outside the
+  // plane are not copied (they are never read as values).
+  __device__ __forceinline__ static bool box_copyable(const void* base, long long pitch_elems) {
+    // 4-byte cp.async needs 4-byte aligned rows: always true for 32-bit
+    // samples; float16 rows need an even element offset
+    return C::ES == 4 ||
+           ((reinterpret_cast<uintptr_t>(base) | (uintptr_t)(pitch_elems * C::ES)) & 3) == 0;
+  }
+  __device__ __forceinline__ void copy_box_row(ST* d, const ST* row, int x0, int pw) const {
+    const ST* g = row + x0;
+    if ((reinterpret_cast<uintptr_t>(g) & 15) == 0) {
+      constexpr int GE = 16 / C::ES;  // elements per group
+#pragma unroll
+      for (int k = 0; k < (C::ROWE / GE + 31) / 32; ++k) {
+        const int gi = lane + 32 * k;
+        const int x = x0 + gi * GE;
+        if (gi < C::ROWE / GE && x >= 0 && x < pw) {
+          if (x + GE <= pw) ptx::cp_async_16(d + gi * GE, g + gi * GE);
+          else ptx::cp_async_16_part(d + gi * GE, g + gi * GE, (uint32_t)((pw - x) * C::ES));
+        }
+      }
+    } else {
+      constexpr int GE = 4 / C::ES;
+#pragma unroll
+      for (int k = 0; k < (C::ROWE / GE + 31) / 32; ++k) {
+        const int gi = lane + 32 * k;
+        const int x = x0 + gi * GE;
+        if (gi < C::ROWE / GE && x >= 0 && x < pw) {
+          if (x + GE <= pw) ptx::cp_async_4(d + gi * GE, g + gi * GE);
+          else ptx::cp_async_4_part(d + gi * GE, g + gi * GE, (uint32_t)((pw - x) * C::ES));
+        }
+      }
+    }
+  }
+
+  // Whether every chunk of this strip is filled in the TMA box layout (by
+  // the TMA engine where it can, by box copies elsewhere): the box must hold
+  // every mirrored column the halo needs, and the planes must allow cp.async.
+  // Border lanes then read remapped columns (remap_cols); otherwise every
+  // lane's elements are filled with their mirrored values directly.
+  __device__ __forceinline__ bool boxed() const {
+    if (a.W < 2 || a.H < 2 || !cols_by_tma()) return false;
+    if constexpr (C::LOAD == SAMPLES) {
+      return box_copyable(a.src[0], a.src_pitch[0]);
+    } else {
+      return box_copyable(a.src[0], a.src_pitch[0]) && box_copyable(a.src[1], a.src_pitch[1]) &&
+             box_copyable(a.src[2], a.src_pitch[2]) && box_copyable(a.src[3], a.src_pitch[3]);
+    }
+  }
+
   __device__ void fill(int c, int s) const {
     const int y0 = yfirst + c * C::CH;
     uint64_t* bar = &bars[s];
@@ -211,7 +268,7 @@ struct Strip {
     const int col = lane_col();
     if constexpr (C::LOAD == SAMPLES) {
       const int sy0 = 2 * y0, xs = 2 * mfirst;
-      if (!tiny && a.src_tma && sy0 >= 0 && sy0 + C::ROWS <= a.H && cols_by_tma()) {
+      if (box && a.src_tma && sy0 >= 0 && sy0 + C::ROWS <= a.H) {
         if (lane == 0) {
           ptx::fence_proxy_async_smem();
           ptx::mbar_arrive_expect_tx(bar, C::BOX_BYTES);
@@ -219,6 +276,16 @@ struct Strip {
         } else {
           ptx::mbar_arrive(bar);
         }
+        return;
+      }
+      if (box) {
+        const ST* src = src_plane(0);
+        const int x0 = align_down(xs, C::A);
+#pragma unroll 1
+        for (int j = 0; j < C::ROWS; ++j)
+          copy_box_row(plane(s, 0) + j * C::ROWE, src + (long long)mirror(sy0 + j, a.H) * a.src_pitch[0], x0,
+                       a.W);
+        ptx::cp_async_arrive(bar);
         return;
       }
       const ST* src = src_plane(0);
@@ -259,7 +326,7 @@ struct Strip {
       ptx::mbar_arrive(bar);
     } else {
       // four subband planes; the lane covers quads mfirst + QL*lane + (0..QL-1)
-      if (!tiny && a.src_tma && y0 >= 0 && y0 + C::CH <= a.fh && cols_by_tma()) {
+      if (box && a.src_tma && y0 >= 0 && y0 + C::CH <= a.fh) {
         if (lane == 0) {
           ptx::fence_proxy_async_smem();
           ptx::mbar_arrive_expect_tx(bar, 4 * C::BOX_BYTES);
@@ -269,6 +336,24 @@ struct Strip {
         } else {
           ptx::mbar_arrive(bar);
         }
+        return;
+      }
+      if (box) {
+        const int x0 = align_down(mfirst, C::A);
+#pragma unroll 1
+        for (int p = 0; p < 4; ++p) {
+          const int py = p >> 1, px = p & 1;
+          const int pw = px ? a.fw : a.cw, ph = py ? a.fh : a.ch;
+#pragma unroll 1
+          for (int r = 0; r < C::CH; ++r) {
+            const int y = y0 + r;
+            // mirroring keeps the parity of a sample index: a mirrored row
+            // of plane p is again a row of plane p
+            const int iy = (y >= 0 && y < ph) ? y : (mirror(2 * y + py, a.H) >> 1);
+            copy_box_row(plane(s, p) + r * C::ROWE, src_plane(p) + (long long)iy * a.src_pitch[p], x0, pw);
+          }
+        }
+        ptx::cp_async_arrive(bar);
         return;
       }
       const bool async = !tiny && C::ES == 4;
@@ -385,7 +470,7 @@ struct Strip {
 
   __device__ __forceinline__ Remap remap_cols() const {
     Remap rm{false, {0u, 0u}, 0u};
-    if (a.W < 2 || a.H < 2 || !a.src_tma || cols_inside() || !cols_by_tma()) return rm;
+    if (!box || cols_inside()) return rm;
     if constexpr (C::LOAD == SAMPLES) {
       const int xs = 2 * mfirst, xal = align_down(xs, C::A), x0 = xs + 2 * QL * lane;
       rm.on = x0 < 0 || x0 + 2 * QL > a.W;
@@ -521,19 +606,18 @@ __device__ __forceinline__ void strip_coords(int s, int ncs, int nrs, int& cs, i
   }
 }
 
-// Lift one strip.  `ring` is the warp's shared-memory ring (nstages stages of
-// C::STAGE_BYTES, whatever stage size the caller reserved is passed as
-// `stage_stride`), `bars` its barriers (initialised for 32 arrivals), and
-// `chunk_ctr` the warp's running count of ring fills: stage and phase of a
-// fill follow from it, so a warp can lift several strips in a row.
-// Returns false if a bounded wait ran out (the launch's status word is set).
+// Lift strip (cs, rs): column strip cs, quad rows [rs*T, rs*T + T).  `ring`
+// is the warp's shared-memory ring (nstages stages; the stage size the
+// caller reserved is passed as `stage_stride`), `bars` its barriers
+// (initialised for 32 arrivals), and `chunk_ctr` the warp's running count of
+// ring fills: stage and phase of a fill follow from it, so a warp can lift
+// several strips in a row.  Returns false if a bounded wait ran out (the
+// launch's status word is set).
 template <class C>
 __device__ __forceinline__ bool run_strip(const LevelArgs& a, const TmaMaps& maps, const Coefs& cf,
-                                          const ConvTaps& ct, int strip, unsigned char* ring,
+                                          const ConvTaps& ct, int cs, int rs, unsigned char* ring,
                                           int stage_stride, uint64_t* bars, uint32_t& chunk_ctr) {
   const int lane = threadIdx.x & 31;
-  int cs, rs;
-  strip_coords(strip, a.ncs, a.nrs, cs, rs);
   const int q0 = rs * a.T;
   const int rows_out = min(a.T, a.ch - q0);
   if (rows_out <= 0) return true;
@@ -541,6 +625,7 @@ __device__ __forceinline__ bool run_strip(const LevelArgs& a, const TmaMaps& map
   using Tot = typename C::Tot;
   Strip<C> sp{a, maps, lane, cs * C::UQ, cs * C::UQ - C::HQ, q0 - Tot::UP, ring, bars};
   sp.stride = stage_stride;
+  sp.box = sp.boxed();
 
   // rows streamed: the strip plus its halo, padded to whole chunks (the
   // extra rows are mirrored image rows, lifted but never stored)
@@ -552,6 +637,7 @@ __device__ __forceinline__ bool run_strip(const LevelArgs& a, const TmaMaps& map
 
   const typename Strip<C>::Out ob = sp.out_bases();
   const typename Strip<C>::Remap remap = sp.remap_cols();
+  const auto coefs = CoefSource<typename C::CSRC>::make(cf);
   Pipe<typename C::VT, C::QL, typename C::PROG> pipe;
   pipe.reset();
   for (int c = 0; c < nchunks; ++c) {
@@ -579,7 +665,7 @@ __device__ __forceinline__ bool run_strip(const LevelArgs& a, const TmaMaps& map
 #pragma unroll 2
     for (int r = 0; r < C::CH; ++r) {
       const Row<typename C::VT, C::QL> in = sp.load_row(s, r, remap);
-      const Row<typename C::VT, C::QL> out = pipe.push(in, cf, ct);
+      const Row<typename C::VT, C::QL> out = pipe.push(in, coefs, ct);
       const int q = qc + r;
       if (q >= q0 && q < q_end) sp.store_row(ob, out, q);
     }
@@ -604,14 +690,23 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, C::MIN_WARPS / kWarpsPerCta
   if (lane == 0) {
     for (int s = 0; s < NS; ++s) ptx::mbar_init(&bars[s], 32);
     ptx::fence_barrier_init();
-    if (a.src_tma) ptx::prefetch_tensormap(&maps.m[0]);
+    if (a.src_tma) {
+      ptx::prefetch_tensormap(&maps.m[0]);
+      if constexpr (C::LOAD == SUBBANDS) {
+        ptx::prefetch_tensormap(&maps.m[1]);
+        ptx::prefetch_tensormap(&maps.m[2]);
+        ptx::prefetch_tensormap(&maps.m[3]);
+      }
+    }
   }
   __syncwarp();
   // the previous level's kernel may still be running: every read and write
   // of level data comes after this point
   ptx::wait_prerequisites();
   uint32_t chunk_ctr = 0;
-  run_strip<C>(a, maps, cf, ct, strip, ring, C::STAGE_BYTES, bars, chunk_ctr);
+  int cs, rs;
+  strip_coords(strip, a.ncs, a.nrs, cs, rs);
+  run_strip<C>(a, maps, cf, ct, cs, rs, ring, C::STAGE_BYTES, bars, chunk_ctr);
 }
 
 // Per-instantiation host glue.

@@ -114,22 +114,75 @@ struct OpShape {
   }
 };
 
+// ---------------------------------------------------------------------------
+// Coefficient sources.  RtCoefs reads a Coefs structure (kernel parameter or
+// batch descriptor): any normalisation, and zero taps / unit scales on an
+// axis of length 1.  StCoefs<WL, INV> holds the wavelet's constants with
+// JPEG 2000 normalisation and both axes longer than one sample as
+// compile-time values, which the compiler folds into the instructions
+// (no registers, no loads).  Both give bit-identical coefficients: the
+// same literals rounded the same way as the host's coefficient tables.
+// ---------------------------------------------------------------------------
+struct RtCoefs {
+  const Coefs& c;
+  __device__ __forceinline__ float p1(int k, int axis) const { return axis ? c.ph1[k] : c.pv1[k]; }
+  __device__ __forceinline__ float p3(int k, int axis) const { return axis ? c.ph3[k] : c.pv3[k]; }
+  __device__ __forceinline__ float u1(int k, int axis) const { return axis ? c.uh1[k] : c.uv1[k]; }
+  __device__ __forceinline__ float u3(int k, int axis) const { return axis ? c.uh3[k] : c.uv3[k]; }
+  __device__ __forceinline__ float scale(int s) const { return c.scale[s]; }
+  __device__ __forceinline__ bool v_on() const { return c.v_on != 0; }
+  __device__ __forceinline__ bool h_on() const { return c.h_on != 0; }
+};
+
+template <int WL, bool INV>
+struct StCoefs {
+  __host__ __device__ constexpr float p1(int k, int) const {
+    return WL == W97 ? float(k == 0 ? kAlpha : kGamma) : WL == W53 ? -0.5f : float(-9.0 / 16.0);
+  }
+  __host__ __device__ constexpr float p3(int, int) const { return WL == WDD ? float(1.0 / 16.0) : 0.0f; }
+  __host__ __device__ constexpr float u1(int k, int) const {
+    return WL == W97 ? float(k == 0 ? kBeta : kDelta) : WL == W53 ? 0.25f : float(9.0 / 32.0);
+  }
+  __host__ __device__ constexpr float u3(int, int) const { return WL == WDD ? float(-1.0 / 32.0) : 0.0f; }
+  // JPEG 2000 band gains: low x 1/K, high x K per axis (K = 1 but for 9/7);
+  // s = LL, HL, LH, HH; the inverse divides
+  __host__ __device__ constexpr float scale(int s) const {
+    const double lo = WL == W97 ? 1.0 / kK97 : 1.0, hi = WL == W97 ? kK97 : 1.0;
+    const double v = ((s & 2) ? hi : lo) * ((s & 1) ? hi : lo);
+    return float(INV ? 1.0 / v : v);
+  }
+  __host__ __device__ constexpr bool v_on() const { return true; }
+  __host__ __device__ constexpr bool h_on() const { return true; }
+};
+
+// Configuration tag of a kernel that reads its coefficients at run time.
+struct RtTag {};
+
+template <class SRC>
+struct CoefSource {
+  __device__ __forceinline__ static SRC make(const Coefs&) { return SRC{}; }
+};
+template <>
+struct CoefSource<RtTag> {
+  __device__ __forceinline__ static RtCoefs make(const Coefs& c) { return RtCoefs{c}; }
+};
+
 // Coefficient of operator OP (pair K, axis: 0 vertical, 1 horizontal) at
 // quad offset OFF.
-template <int DEG, int OP, int K, int AXIS, int OFF>
-__device__ __forceinline__ float op_tap(const Coefs& c) {
-  const float p1 = AXIS ? c.ph1[K] : c.pv1[K];
-  const float u1 = AXIS ? c.uh1[K] : c.uv1[K];
+template <int DEG, int OP, int K, int AXIS, int OFF, class CS>
+__device__ __forceinline__ float op_tap(const CS& c) {
+  const float p1 = c.p1(K, AXIS);
+  const float u1 = c.u1(K, AXIS);
   if constexpr (OP == OP_I) {
     return 1.0f;
   } else if constexpr (OP == OP_P || OP == OP_P1) {
     if constexpr (DEG == 1) return p1;
-    else return (OFF == 0 || OFF == 1) ? p1 : (AXIS ? c.ph3[K] : c.pv3[K]);
+    else return (OFF == 0 || OFF == 1) ? p1 : c.p3(K, AXIS);
   } else if constexpr (OP == OP_P0) {
     return p1;
   } else if constexpr (OP == OP_U || OP == OP_U1) {
     if constexpr (DEG == 1) return u1;
-    else return (OFF == -1 || OFF == 0) ? u1 : (AXIS ? c.uh3[K] : c.uv3[K]);
+    else return (OFF == -1 || OFF == 0) ? u1 : c.u3(K, AXIS);
   } else if constexpr (OP == OP_U0) {
     return u1;
   } else if constexpr (OP == OP_V) {  // V = PU + 1: pu z^-1 + (1 + 2pu) + pu z
@@ -162,9 +215,8 @@ struct Lin {
   // roundings at the magnitude of the target than one FMA per tap.  The
   // class holding the centre tap, whose coefficient is the largest in the
   // products of V, is accumulated in the second pass, after all others.
-  template <class T, bool CENTRE_PASS, int QL>
-  __device__ __forceinline__ static void term(const Row<float, QL>* w, Row<float, QL>& o,
-                                              const Coefs& c) {
+  template <class T, bool CENTRE_PASS, int QL, class CS>
+  __device__ __forceinline__ static void term(const Row<float, QL>* w, Row<float, QL>& o, const CS& c) {
     using VS = OpShape<DEG, T::vop>;
     using HS = OpShape<DEG, T::hop>;
     static_for<0, VS::NCLS - 1>([&](auto cvi) {
@@ -195,8 +247,8 @@ struct Lin {
               });
             }
           });
-          const float cf = (T::sgn > 0 ? 1.0f : -1.0f) * op_tap<DEG, T::vop, K, 0, VS::rep(CV)>(c) *
-                           op_tap<DEG, T::hop, K, 1, HS::rep(CH)>(c);
+          const float cf = (T::sgn > 0 ? 1.0f : -1.0f) * op_tap<DEG, T::vop, K, 0, VS::rep(CV), CS>(c) *
+                           op_tap<DEG, T::hop, K, 1, HS::rep(CH), CS>(c);
 #pragma unroll
           for (int j = 0; j < QL; ++j) o.s[T::tgt][j] = fmaf(cf, s[j], o.s[T::tgt][j]);
         }
@@ -204,9 +256,9 @@ struct Lin {
     });
   }
 
-  template <int QL>
-  __device__ __forceinline__ static void eval(const Row<float, QL>* w, Row<float, QL>& o,
-                                              const Coefs& c, const ConvTaps&) {
+  template <int QL, class CS>
+  __device__ __forceinline__ static void eval(const Row<float, QL>* w, Row<float, QL>& o, const CS& c,
+                                              const ConvTaps&) {
     o = w[UP];
     if constexpr (REPLACE) {
 #pragma unroll
@@ -215,21 +267,21 @@ struct Lin {
 #pragma unroll
           for (int j = 0; j < QL; ++j) o.s[s][j] = 0.0f;
     }
-    (term<Ts, false, QL>(w, o, c), ...);
-    (term<Ts, true, QL>(w, o, c), ...);
+    (term<Ts, false, QL, CS>(w, o, c), ...);
+    (term<Ts, true, QL, CS>(w, o, c), ...);
   }
 };
 
 // Scaling step (Sec. 2.2, the diagonal matrix of M): per-subband factors.
 struct Scale {
   static constexpr int UP = 0, DOWN = 0, LEFT = 0, RIGHT = 0;
-  template <int QL>
-  __device__ __forceinline__ static void eval(const Row<float, QL>* w, Row<float, QL>& o,
-                                              const Coefs& c, const ConvTaps&) {
+  template <int QL, class CS>
+  __device__ __forceinline__ static void eval(const Row<float, QL>* w, Row<float, QL>& o, const CS& c,
+                                              const ConvTaps&) {
 #pragma unroll
     for (int s = 0; s < 4; ++s)
 #pragma unroll
-      for (int j = 0; j < QL; ++j) o.s[s][j] = w[0].s[s][j] * c.scale[s];
+      for (int j = 0; j < QL; ++j) o.s[s][j] = w[0].s[s][j] * c.scale(s);
   }
 };
 
@@ -261,9 +313,9 @@ struct Conv {
   static constexpr int DOWN = cmax(cmax(S::hi(0, 0), S::hi(0, 1)), cmax(S::hi(1, 0), S::hi(1, 1)));
   static constexpr int LEFT = UP, RIGHT = DOWN;
 
-  template <int QL>
-  __device__ __forceinline__ static void eval(const Row<float, QL>* w, Row<float, QL>& o,
-                                              const Coefs&, const ConvTaps& t) {
+  template <int QL, class CS>
+  __device__ __forceinline__ static void eval(const Row<float, QL>* w, Row<float, QL>& o, const CS&,
+                                              const ConvTaps& t) {
     static_for<0, 3>([&](auto so_sx) {
       constexpr int SO = decltype(so_sx)::value >> 1, SX = decltype(so_sx)::value & 1;
       float acc[QL];
@@ -303,13 +355,13 @@ struct Int53 {
   static constexpr int LEFT = KIND == 3 ? 1 : 0;
   static constexpr int RIGHT = KIND == 2 ? 1 : 0;
 
-  template <int QL>
-  __device__ __forceinline__ static void eval(const Row<int, QL>* w, Row<int, QL>& o,
-                                              const Coefs& c, const ConvTaps&) {
+  template <int QL, class CS>
+  __device__ __forceinline__ static void eval(const Row<int, QL>* w, Row<int, QL>& o, const CS& c,
+                                              const ConvTaps&) {
     o = w[UP];
     const int sg = INV ? -1 : 1;
     if constexpr (KIND == 0) {  // odd rows -= floor((even above + even below) / 2)
-      if (c.v_on) {
+      if (c.v_on()) {
 #pragma unroll
         for (int j = 0; j < QL; ++j) {
           o.s[LH][j] -= sg * ((w[0].s[LL][j] + w[1].s[LL][j]) >> 1);
@@ -317,7 +369,7 @@ struct Int53 {
         }
       }
     } else if constexpr (KIND == 1) {  // even rows += floor((odd above + odd below + 2) / 4)
-      if (c.v_on) {
+      if (c.v_on()) {
 #pragma unroll
         for (int j = 0; j < QL; ++j) {
           o.s[LL][j] += sg * ((w[0].s[LH][j] + w[1].s[LH][j] + 2) >> 2);
@@ -325,7 +377,7 @@ struct Int53 {
         }
       }
     } else if constexpr (KIND == 2) {  // odd columns from the even ones at m, m+1
-      if (c.h_on) {
+      if (c.h_on()) {
         const int llr = hpos<QL>(w[0].s[LL]), lhr = hpos<QL>(w[0].s[LH]);
 #pragma unroll
         for (int j = 0; j < QL; ++j) {
@@ -336,7 +388,7 @@ struct Int53 {
         }
       }
     } else {  // even columns from the odd ones at m-1, m
-      if (c.h_on) {
+      if (c.h_on()) {
         const int hll = hpos<-1>(w[0].s[HL]), hhl = hpos<-1>(w[0].s[HH]);
 #pragma unroll
         for (int j = 0; j < QL; ++j) {
@@ -382,7 +434,8 @@ struct Pipe;
 template <typename V, int QL>
 struct Pipe<V, QL, List<>> {
   __device__ __forceinline__ void reset() {}
-  __device__ __forceinline__ Row<V, QL> push(const Row<V, QL>& r, const Coefs&, const ConvTaps&) {
+  template <class CS>
+  __device__ __forceinline__ Row<V, QL> push(const Row<V, QL>& r, const CS&, const ConvTaps&) {
     return r;
   }
 };
@@ -403,8 +456,8 @@ struct Pipe<V, QL, List<S0, S...>> {
     rest.reset();
   }
 
-  __device__ __forceinline__ Row<V, QL> push(const Row<V, QL>& r, const Coefs& c,
-                                             const ConvTaps& t) {
+  template <class CS>
+  __device__ __forceinline__ Row<V, QL> push(const Row<V, QL>& r, const CS& c, const ConvTaps& t) {
 #pragma unroll
     for (int k = 0; k + 1 < NW; ++k) win[k] = win[k + 1];
     win[NW - 1] = r;
