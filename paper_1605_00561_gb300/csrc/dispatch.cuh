@@ -19,25 +19,30 @@ inline bool run(int nstages, KernelInfo* info, const LaunchCall* call, cudaError
   return true;
 }
 
-// Quadruples per lane: four for the light schemes (128-bit vectors, fewer
-// instructions per pixel); two for the schemes whose windows or stencils
-// would otherwise exceed the register file (Polyphase, Convolution, and the
-// three-step schemes of two pairs).  A ring stage holds the same bytes
-// either way.
+// Quadruples per lane: four (128-bit vectors, fewer instructions and
+// shuffles per sample) except for Convolution and the unstarred Polyphase,
+// whose windows and stencils at four exceed the register file (and, for
+// Polyphase with two pairs, what the compiler handles).  A ring stage holds
+// the same bytes either way.
 template <int SCHEME, int WL>
-constexpr int kQuadsPerLane =
-    (SCHEME == POLYPHASE || SCHEME == POLYPHASE_S || SCHEME == CONVOLUTION ||
-     (WL == W97 && (SCHEME == IWAHASHI || SCHEME == IWAHASHI_S || SCHEME == EXPLOSIVE ||
-                    SCHEME == EXPLOSIVE_S)))
-        ? 2
-        : 4;
+constexpr int kQuadsPerLane = (SCHEME == POLYPHASE || SCHEME == CONVOLUTION) ? 2 : 4;
+
+// Resident warps per SM the register budget is cut for: 16 (128 registers)
+// in general; 12 (168 registers) for the three-step schemes with two pairs,
+// which need them at four quadruples per lane; 8 for Convolution.
+template <int SCHEME, int WL>
+constexpr int kMinWarps =
+    SCHEME == CONVOLUTION ? 8
+    : (WL == W97 && (SCHEME == IWAHASHI || SCHEME == IWAHASHI_S || SCHEME == EXPLOSIVE || SCHEME == EXPLOSIVE_S))
+        ? 12
+        : 16;
 
 // STATIC: coefficients folded in at compile time (StCoefs), for levels with
 // JPEG 2000 normalisation and both axes longer than one sample.
 template <int SCHEME, int WL, typename ST, bool INV, bool STATIC = false>
 using FusedCfg = Cfg<ST, float, typename FusedProgram<SCHEME, WL, INV>::type, INV ? SUBBANDS : SAMPLES,
                      INV ? SAMPLES : SUBBANDS, kQuadsPerLane<SCHEME, WL>, 8 / kQuadsPerLane<SCHEME, WL>,
-                     SCHEME == CONVOLUTION ? 8 : 16, std::conditional_t<STATIC, StCoefs<WL, INV>, RtTag>>;
+                     kMinWarps<SCHEME, WL>, std::conditional_t<STATIC, StCoefs<WL, INV>, RtTag>>;
 
 template <int SCHEME, int WL, typename ST, bool STATIC>
 inline bool fused_dir(bool inv, int ns, KernelInfo* info, const LaunchCall* call, cudaError_t* err) {

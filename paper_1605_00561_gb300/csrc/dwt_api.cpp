@@ -291,12 +291,30 @@ size_t elem_size(int dtype) { return dtype == F16S ? 2 : 4; }
 // Quad rows per strip.  Strips of about ten rows keep several waves of
 // one-warp blocks in flight, so the block scheduler balances SMs that
 // progress at different rates, while the vertical halo re-reads hit L2
-// (vertically adjacent strips run at the same time).  A level too small to
-// fill one wave at that height gets shorter strips, down to two rows.
-int strip_height(int target, int ch, int ncs, int cap_warps) {
-  const long long one_wave = ((long long)ch * ncs + cap_warps - 1) / cap_warps;
-  return (int)std::max<long long>(2, std::min<long long>(target, one_wave));
+// (vertically adjacent strips run at the same time).  A level that fills
+// the GPU fewer than four times at that height is governed by its last
+// wave: it takes the height (2..32 rows) that minimises the number of waves
+// times the rows each strip streams (its own, the halo `halo` and the
+// padding to whole chunks of `chunk` rows).
+int strip_height(int target, int ch, int ncs, int cap_warps, int halo, int chunk) {
+  auto strips = [&](int T) { return (long long)ncs * ((ch + T - 1) / T); };
+  if (strips(target) >= 4LL * cap_warps) return target;
+  int best = 2;
+  long long best_cost = -1;
+  for (int T = 2; T <= 32; ++T) {
+    const long long waves = (strips(T) + cap_warps - 1) / cap_warps;
+    const long long rows = ((std::min(T, ch) + halo + chunk - 1) / chunk) * chunk;
+    const long long cost = waves * rows;
+    if (best_cost < 0 || cost < best_cost) {
+      best = T;
+      best_cost = cost;
+    }
+  }
+  return best;
 }
+
+// Chunk rows (quad rows per ring stage) of a kernel.
+int chunk_rows(const KernelInfo& ki) { return ki.load == SAMPLES ? ki.box_h / 2 : ki.box_h; }
 
 size_t round_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
@@ -480,7 +498,7 @@ dwt_status launch(dwt_plan_s* p, const LaunchKey& key, LevelArgs& a, const Coefs
   // one strip per resident warp when the level is large enough: a single
   // wave, with strips as tall as that allows (less vertical halo)
   a.ncs = (a.cw + ki.uq - 1) / ki.uq;
-  a.T = strip_height(p->strip_rows, a.ch, a.ncs, cap);
+  a.T = strip_height(p->strip_rows, a.ch, a.ncs, cap, ki.up + ki.down, chunk_rows(ki));
   a.nrs = (a.ch + a.T - 1) / a.T;
   // a level that does not fill the GPU once is latency-bound: a deeper
   // ring lets each (short) strip issue all its chunk loads at once, as long
@@ -870,7 +888,7 @@ dwt_status batch_submit(const dwt_request* reqs, int n, cudaStream_t s, int* d_s
       LevelArgs& a = b.a;
       level_dims(p, k, a);
       a.ncs = (a.cw + ki.uq - 1) / ki.uq;
-      a.T = strip_height(p->strip_rows, a.ch, a.ncs, cap);
+      a.T = strip_height(p->strip_rows, a.ch, a.ncs, cap, ki.up + ki.down, chunk_rows(ki));
       a.nrs = (a.ch + a.T - 1) / a.T;
       a.nstages = nstages;
       b.cf = make_coefs(lifting_of(p->wavelet), p->norm, a.W, a.H, PASS_FUSED, inverse);
@@ -1185,7 +1203,7 @@ dwt_status forward_on_scratch(int w, int h, int wavelet, int levels, int dtype, 
       per_sm = 1;
     const int cap = std::max(sms, 1) * std::max(per_sm, 1);
     a.ncs = (a.cw + ki.uq - 1) / ki.uq;
-    a.T = strip_height(kDefaultStripRows, a.ch, a.ncs, cap);
+    a.T = strip_height(kDefaultStripRows, a.ch, a.ncs, cap, ki.up + ki.down, chunk_rows(ki));
     a.nrs = (a.ch + a.T - 1) / a.T;
     a.nstages = (long long)a.ncs * a.nrs < cap ? kMaxStages : kDefaultStages;
     a.status = d_status;

@@ -6,8 +6,8 @@ namespace dwt {
 
 bool group_explosive(const LaunchKey& k, int ns, KernelInfo* info, const LaunchCall* call,
                    cudaError_t* err) {
-  if (dev::fused_float<EXPLOSIVE>(k, ns, info, call, err)) return true;
-  if (dev::fused_float<EXPLOSIVE_S>(k, ns, info, call, err)) return true;
+  if (dev::fused_float<EXPLOSIVE, true>(k, ns, info, call, err)) return true;
+  if (dev::fused_float<EXPLOSIVE_S, true>(k, ns, info, call, err)) return true;
   return false;
 }
 

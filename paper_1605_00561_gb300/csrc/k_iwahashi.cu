@@ -6,8 +6,8 @@ namespace dwt {
 
 bool group_iwahashi(const LaunchKey& k, int ns, KernelInfo* info, const LaunchCall* call,
                    cudaError_t* err) {
-  if (dev::fused_float<IWAHASHI>(k, ns, info, call, err)) return true;
-  if (dev::fused_float<IWAHASHI_S>(k, ns, info, call, err)) return true;
+  if (dev::fused_float<IWAHASHI, true>(k, ns, info, call, err)) return true;
+  if (dev::fused_float<IWAHASHI_S, true>(k, ns, info, call, err)) return true;
   return false;
 }
 

@@ -6,7 +6,7 @@ namespace dwt {
 
 bool group_monolithic(const LaunchKey& k, int ns, KernelInfo* info, const LaunchCall* call,
                    cudaError_t* err) {
-  if (dev::fused_float<MONOLITHIC>(k, ns, info, call, err)) return true;
+  if (dev::fused_float<MONOLITHIC, true>(k, ns, info, call, err)) return true;
   if (dev::fused_float<MONOLITHIC_S, true>(k, ns, info, call, err)) return true;
   return false;
 }

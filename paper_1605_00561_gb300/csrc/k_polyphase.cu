@@ -7,7 +7,7 @@ namespace dwt {
 bool group_polyphase(const LaunchKey& k, int ns, KernelInfo* info, const LaunchCall* call,
                    cudaError_t* err) {
   if (dev::fused_float<POLYPHASE>(k, ns, info, call, err)) return true;
-  if (dev::fused_float<POLYPHASE_S>(k, ns, info, call, err)) return true;
+  if (dev::fused_float<POLYPHASE_S, true>(k, ns, info, call, err)) return true;
   return false;
 }
 
