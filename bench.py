@@ -80,9 +80,9 @@ def workload_name(a):
 LEVEL_KERNEL_SOURCES = ["dwt_internal.h", "ptx.cuh", "stages.cuh", "programs.cuh", "level_kernel.cuh",
                         "dispatch.cuh"]
 SCHEME_SOURCE = {"rowcol": "k_rowcol.cu", "sweldens": "k_sweldens.cu", "iwahashi": "k_iwahashi.cu",
-                 "iwahashi*": "k_iwahashi.cu", "explosive": "k_explosive.cu", "explosive*": "k_explosive.cu",
-                 "monolithic": "k_monolithic.cu", "monolithic*": "k_monolithic.cu",
-                 "polyphase": "k_polyphase.cu", "polyphase*": "k_polyphase.cu", "convolution": "k_convolution.cu"}
+                 "iwahashi*": "k_iwahashi_s.cu", "explosive": "k_explosive.cu", "explosive*": "k_explosive_s.cu",
+                 "monolithic": "k_monolithic.cu", "monolithic*": "k_monolithic_s.cu",
+                 "polyphase": "k_polyphase.cu", "polyphase*": "k_polyphase_s.cu", "convolution": "k_convolution.cu"}
 
 
 def kernel_source_hash(scheme="monolithic*"):

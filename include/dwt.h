@@ -60,7 +60,8 @@ typedef enum {
 typedef enum {
   DWT_CDF53 = 0, /* P = -1/2 (1 + z^-1), U = 1/4 (1 + z) (Sec. 5)                  */
   DWT_CDF97 = 1, /* two pairs (alpha, beta), (gamma, delta) (Sec. 5)              */
-  DWT_DD137 = 2  /* Deslauriers-Dubuc (4,4): degree-3 P and U (Sec. 5)            */
+  DWT_DD137 = 2  /* Deslauriers-Dubuc 13/7: degree-3 P and U (Sec. 5); float32, all
+                    schemes but Polyphase(*) and Convolution                       */
 } dwt_wavelet;
 
 typedef enum {
@@ -93,7 +94,7 @@ typedef enum { DWT_NORM_JPEG2000 = 0, DWT_NORM_ZETA = 1 } dwt_norm;
  * device memory and are cheap to create and destroy.  Errors: DWT_EINVAL for w < 1, h < 1,
  * levels < 0, levels above the number of halvings until both dimensions
  * are 1, or out == NULL; DWT_EUNSUPPORTED for DWT_I32 with a wavelet other
- * than 5/3; DWT_ENOMEM; DWT_ECUDA. */
+ * than 5/3 and for DWT_DD137 with a storage type other than DWT_F32; DWT_ENOMEM; DWT_ECUDA. */
 dwt_status dwt_plan_create(int w, int h, dwt_wavelet wavelet, int levels, dwt_dtype dtype,
                            dwt_plan* out);
 

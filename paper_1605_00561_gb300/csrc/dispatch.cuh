@@ -37,6 +37,12 @@ constexpr int kMinWarps =
         ? 12
         : 16;
 
+// Schemes whose steps stay stencils of the lifting operators themselves and
+// so take the degree-3 DD 13/7 pair; Polyphase and Convolution would need
+// the degree-6 products.
+template <int SCHEME>
+constexpr bool kHasDegree3 = SCHEME != POLYPHASE && SCHEME != POLYPHASE_S && SCHEME != CONVOLUTION;
+
 // STATIC: coefficients folded in at compile time (StCoefs), for levels with
 // JPEG 2000 normalisation and both axes longer than one sample.
 template <int SCHEME, int WL, typename ST, bool INV, bool STATIC = false>
@@ -68,6 +74,12 @@ inline bool fused_float(const LaunchKey& k, int ns, KernelInfo* info, const Laun
   }
   if (k.wavelet == W53 && k.dtype == F32) return fused_dir<SCHEME, W53, float, false>(inv, ns, info, call, err);
   if (k.wavelet == W97 && k.dtype == F32) return fused_dir<SCHEME, W97, float, false>(inv, ns, info, call, err);
+  if constexpr (kHasDegree3<SCHEME>) {
+    if (k.wavelet == WDD && k.dtype == F32) {
+      if (WITH_STATIC && k.static_coefs) return fused_dir<SCHEME, WDD, float, true>(inv, ns, info, call, err);
+      return fused_dir<SCHEME, WDD, float, false>(inv, ns, info, call, err);
+    }
+  }
   if (k.wavelet == W53 && k.dtype == F16S) return fused_dir<SCHEME, W53, __half, false>(inv, ns, info, call, err);
   if (k.wavelet == W97 && k.dtype == F16S) return fused_dir<SCHEME, W97, __half, false>(inv, ns, info, call, err);
   return false;

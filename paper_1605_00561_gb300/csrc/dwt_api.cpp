@@ -197,8 +197,9 @@ bool conv_taps(const Lifting& L, int norm, int Wk, int Hk, bool inverse, ConvTap
 // ---------------------------------------------------------------------------
 // Kernel lookup, geometry, TMA
 // ---------------------------------------------------------------------------
-const GroupFn kGroups[] = {group_sweldens, group_iwahashi, group_explosive, group_monolithic,
-                           group_polyphase, group_convolution, group_rowcol};
+const GroupFn kGroups[] = {group_sweldens,   group_iwahashi,   group_iwahashi_s,  group_explosive,
+                           group_explosive_s, group_monolithic, group_monolithic_s, group_polyphase,
+                           group_polyphase_s, group_convolution, group_rowcol};
 
 bool find_kernel(const LaunchKey& k, int ns, KernelInfo* info) {
   for (GroupFn g : kGroups) {
@@ -424,8 +425,12 @@ int default_scheme(const dwt_plan_s* p) {
 
 bool scheme_supported(int wavelet, int dtype, int scheme) {
   if (scheme <= DWT_AUTO || scheme >= NUM_SCHEMES) return false;
-  if (wavelet == DWT_DD137) return false;
   if (dtype == DWT_I32) return wavelet == DWT_CDF53 && (scheme == DWT_ROWCOL || scheme == DWT_SWELDENS);
+  // DD 13/7 (degree-3 pairs): float32, and only the schemes whose steps are
+  // stencils of P and U themselves (Polyphase and Convolution would need
+  // the degree-6 products)
+  if (wavelet == DWT_DD137)
+    return dtype == DWT_F32 && scheme != DWT_POLYPHASE && scheme != DWT_POLYPHASE_S && scheme != DWT_CONVOLUTION;
   return true;
 }
 
@@ -1252,7 +1257,7 @@ dwt_status dwt_plan_create(int w, int h, dwt_wavelet wavelet, int levels, dwt_dt
   for (int a = w, b = h; a > 1 || b > 1; a = (a + 1) / 2, b = (b + 1) / 2) ++maxl;
   if (levels > maxl) return DWT_EINVAL;
   if (dtype == DWT_I32 && wavelet != DWT_CDF53) return DWT_EUNSUPPORTED;
-  if (wavelet == DWT_DD137) return DWT_EUNSUPPORTED;
+  if (wavelet == DWT_DD137 && dtype != DWT_F32) return DWT_EUNSUPPORTED;
   dwt_plan_s* p = new (std::nothrow) dwt_plan_s();
   if (!p) return DWT_ENOMEM;
   p->w = w;

@@ -121,9 +121,13 @@ using GroupFn = bool (*)(const LaunchKey& k, int nstages, KernelInfo* info, cons
 
 bool group_sweldens(const LaunchKey&, int, KernelInfo*, const LaunchCall*, cudaError_t*);
 bool group_iwahashi(const LaunchKey&, int, KernelInfo*, const LaunchCall*, cudaError_t*);
+bool group_iwahashi_s(const LaunchKey&, int, KernelInfo*, const LaunchCall*, cudaError_t*);
 bool group_explosive(const LaunchKey&, int, KernelInfo*, const LaunchCall*, cudaError_t*);
+bool group_explosive_s(const LaunchKey&, int, KernelInfo*, const LaunchCall*, cudaError_t*);
 bool group_monolithic(const LaunchKey&, int, KernelInfo*, const LaunchCall*, cudaError_t*);
+bool group_monolithic_s(const LaunchKey&, int, KernelInfo*, const LaunchCall*, cudaError_t*);
 bool group_polyphase(const LaunchKey&, int, KernelInfo*, const LaunchCall*, cudaError_t*);
+bool group_polyphase_s(const LaunchKey&, int, KernelInfo*, const LaunchCall*, cudaError_t*);
 bool group_convolution(const LaunchKey&, int, KernelInfo*, const LaunchCall*, cudaError_t*);
 bool group_rowcol(const LaunchKey&, int, KernelInfo*, const LaunchCall*, cudaError_t*);
 

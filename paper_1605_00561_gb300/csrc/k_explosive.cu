@@ -1,14 +1,11 @@
-// Kernels of the EXPLOSIVE and EXPLOSIVE_S scheme(s): forward and inverse, CDF 5/3 and 9/7,
-// float32 and float16-storage.
+// Kernels of the Explosive (Sec. 3.1) scheme: forward and inverse, every wavelet and
+// storage type the scheme supports.
 #include "dispatch.cuh"
 
 namespace dwt {
 
-bool group_explosive(const LaunchKey& k, int ns, KernelInfo* info, const LaunchCall* call,
-                   cudaError_t* err) {
-  if (dev::fused_float<EXPLOSIVE, true>(k, ns, info, call, err)) return true;
-  if (dev::fused_float<EXPLOSIVE_S, true>(k, ns, info, call, err)) return true;
-  return false;
+bool group_explosive(const LaunchKey& k, int ns, KernelInfo* info, const LaunchCall* call, cudaError_t* err) {
+  return dev::fused_float<EXPLOSIVE, true>(k, ns, info, call, err);
 }
 
 }  // namespace dwt

@@ -1,0 +1,11 @@
+// Kernels of the Explosive* (Sec. 3.1 with the split of Sec. 4) scheme: forward and
+// inverse, every wavelet and storage type the scheme supports.
+#include "dispatch.cuh"
+
+namespace dwt {
+
+bool group_explosive_s(const LaunchKey& k, int ns, KernelInfo* info, const LaunchCall* call, cudaError_t* err) {
+  return dev::fused_float<EXPLOSIVE_S, true>(k, ns, info, call, err);
+}
+
+}  // namespace dwt

@@ -1,0 +1,11 @@
+// Kernels of the Iwahashi* (Sec. 2.6 with the split of Sec. 4) scheme: forward and
+// inverse, every wavelet and storage type the scheme supports.
+#include "dispatch.cuh"
+
+namespace dwt {
+
+bool group_iwahashi_s(const LaunchKey& k, int ns, KernelInfo* info, const LaunchCall* call, cudaError_t* err) {
+  return dev::fused_float<IWAHASHI_S, true>(k, ns, info, call, err);
+}
+
+}  // namespace dwt

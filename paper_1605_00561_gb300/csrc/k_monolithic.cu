@@ -1,14 +1,11 @@
-// Kernels of the MONOLITHIC and MONOLITHIC_S scheme(s): forward and inverse, CDF 5/3 and 9/7,
-// float32 and float16-storage.
+// Kernels of the Monolithic (Sec. 3.2) scheme: forward and inverse, every wavelet and
+// storage type the scheme supports.
 #include "dispatch.cuh"
 
 namespace dwt {
 
-bool group_monolithic(const LaunchKey& k, int ns, KernelInfo* info, const LaunchCall* call,
-                   cudaError_t* err) {
-  if (dev::fused_float<MONOLITHIC, true>(k, ns, info, call, err)) return true;
-  if (dev::fused_float<MONOLITHIC_S, true>(k, ns, info, call, err)) return true;
-  return false;
+bool group_monolithic(const LaunchKey& k, int ns, KernelInfo* info, const LaunchCall* call, cudaError_t* err) {
+  return dev::fused_float<MONOLITHIC, true>(k, ns, info, call, err);
 }
 
 }  // namespace dwt

@@ -1,0 +1,11 @@
+// Kernels of the Monolithic* (Sec. 3.2 with the split of Sec. 4) scheme: forward and
+// inverse, every wavelet and storage type the scheme supports.
+#include "dispatch.cuh"
+
+namespace dwt {
+
+bool group_monolithic_s(const LaunchKey& k, int ns, KernelInfo* info, const LaunchCall* call, cudaError_t* err) {
+  return dev::fused_float<MONOLITHIC_S, true>(k, ns, info, call, err);
+}
+
+}  // namespace dwt

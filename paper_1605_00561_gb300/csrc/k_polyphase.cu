@@ -1,14 +1,11 @@
-// Kernels of the POLYPHASE and POLYPHASE_S scheme(s): forward and inverse, CDF 5/3 and 9/7,
-// float32 and float16-storage.
+// Kernels of the Polyphase (Sec. 2.3) scheme: forward and inverse, every wavelet and
+// storage type the scheme supports.
 #include "dispatch.cuh"
 
 namespace dwt {
 
-bool group_polyphase(const LaunchKey& k, int ns, KernelInfo* info, const LaunchCall* call,
-                   cudaError_t* err) {
-  if (dev::fused_float<POLYPHASE>(k, ns, info, call, err)) return true;
-  if (dev::fused_float<POLYPHASE_S, true>(k, ns, info, call, err)) return true;
-  return false;
+bool group_polyphase(const LaunchKey& k, int ns, KernelInfo* info, const LaunchCall* call, cudaError_t* err) {
+  return dev::fused_float<POLYPHASE>(k, ns, info, call, err);
 }
 
 }  // namespace dwt

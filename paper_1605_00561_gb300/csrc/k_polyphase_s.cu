@@ -1,0 +1,11 @@
+// Kernels of the Polyphase* (Sec. 2.3 with the split of Sec. 4) scheme: forward and
+// inverse, every wavelet and storage type the scheme supports.
+#include "dispatch.cuh"
+
+namespace dwt {
+
+bool group_polyphase_s(const LaunchKey& k, int ns, KernelInfo* info, const LaunchCall* call, cudaError_t* err) {
+  return dev::fused_float<POLYPHASE_S, true>(k, ns, info, call, err);
+}
+
+}  // namespace dwt

@@ -35,6 +35,9 @@ bool pass_switch(const LaunchKey& k, int ns, KernelInfo* info, const LaunchCall*
   if (k.wavelet == W97 && k.dtype == F32)
     return inv ? dev::run<FloatPass<PASS, W97, float, true>>(ns, info, call, err)
                : dev::run<FloatPass<PASS, W97, float, false>>(ns, info, call, err);
+  if (k.wavelet == WDD && k.dtype == F32)
+    return inv ? dev::run<FloatPass<PASS, WDD, float, true>>(ns, info, call, err)
+               : dev::run<FloatPass<PASS, WDD, float, false>>(ns, info, call, err);
   if (k.wavelet == W53 && k.dtype == F16S)
     return inv ? dev::run<FloatPass<PASS, W53, __half, true>>(ns, info, call, err)
                : dev::run<FloatPass<PASS, W53, __half, false>>(ns, info, call, err);

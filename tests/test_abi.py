@@ -54,6 +54,11 @@ def test_invalid_arguments_rejected_before_any_cuda_call(libdwt):
     assert lib.dwt_plan_create(4, 4, 7, 1, 0, ctypes.byref(out)) == libdwt.DWT_EINVAL
     assert lib.dwt_plan_create(4, 4, libdwt.DWT_CDF97, 1, libdwt.DWT_I32, ctypes.byref(out)) == \
         libdwt.DWT_EUNSUPPORTED
+    # DD 13/7 runs in float32 only
+    assert lib.dwt_plan_create(4, 4, libdwt.DWT_DD137, 1, libdwt.DWT_F16S, ctypes.byref(out)) == \
+        libdwt.DWT_EUNSUPPORTED
+    assert lib.dwt_plan_create(4, 4, libdwt.DWT_DD137, 1, libdwt.DWT_I32, ctypes.byref(out)) == \
+        libdwt.DWT_EUNSUPPORTED
     assert lib.dwt_plan_create(4, 4, 0, 1, 0, None) == libdwt.DWT_EINVAL
     assert lib.dwt2_forward(None, None, 0, None, 0, None) == libdwt.DWT_EINVAL
     assert lib.dwt_plan_destroy(None) == libdwt.DWT_EINVAL

@@ -67,6 +67,39 @@ def test_float32_forward_inverse_vs_oracle(dwt, scheme, wavelet, h, w, L):
     assert np.abs(y - x).max() <= TOL_ROUND_TRIP, "round trip"
 
 
+# DD 13/7 (degree-3 predict and update, Sec. 5): the schemes whose steps are
+# stencils of P and U themselves (Polyphase and Convolution are refused)
+DD_SCHEMES = ["rowcol", "sweldens", "iwahashi", "iwahashi*", "explosive", "explosive*", "monolithic",
+              "monolithic*"]
+
+
+@pytest.mark.parametrize("scheme", DD_SCHEMES)
+@pytest.mark.parametrize("h,w,L", SHAPES)
+def test_dd137_forward_inverse_vs_oracle(dwt, scheme, h, w, L):
+    x = inputs.uniform_image(h, w, seed=h * 31 + w)
+    ref = oracle.dwt2(x.astype(np.float64), oracle.DD137, L)
+    c, y, yo = run_fwd_inv(dwt, x, "dd137", L, "f32", scheme, coef_in=ref.astype(np.float32))
+    assert np.abs(c - ref).max() <= TOL_F32, "forward"
+    assert np.abs(yo - x).max() <= TOL_F32, "inverse of oracle coefficients"
+    assert np.abs(y - x).max() <= TOL_ROUND_TRIP, "round trip"
+
+
+def test_dd137_unsupported_combinations(dwt):
+    p = dwt.dwt_plan_create(64, 64, dwt.DWT_DD137, 2, dwt.DWT_F32)
+    for name in ("polyphase", "polyphase*", "convolution"):
+        with pytest.raises(dwt.DwtError) as e:
+            dwt.dwt_plan_set_scheme(p, dwt.SCHEMES[name])
+        assert e.value.status == dwt.DWT_EUNSUPPORTED
+    # the batch kernel holds no DD 13/7 kind
+    x = torch.zeros(64, 64, device="cuda")
+    y = torch.empty_like(x)
+    req = dwt.DwtRequest(p, x.data_ptr(), 256, y.data_ptr(), 256, 0)
+    with pytest.raises(dwt.DwtError) as e:
+        dwt.dwt_batch_submit([req])
+    assert e.value.status == dwt.DWT_EUNSUPPORTED
+    dwt.dwt_plan_destroy(p)
+
+
 @pytest.mark.parametrize("scheme", ["rowcol", "sweldens"])
 @pytest.mark.parametrize("h,w,L", SHAPES + [(333, 500, 5)])
 def test_int32_bit_exact(dwt, scheme, h, w, L):
