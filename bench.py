@@ -9,7 +9,8 @@ Inputs (268 MB per buffer) are larger than L2 (129 MB), so no L2 flush is
 needed between steps.
 
 ``--impl reference`` times the oracle (plain C, FP64) on the host cores on a
-bounded sample of the same workload (a 1024^2 image per step).
+bounded sample of the same workload (a square image per step, at most
+1024^2, sized so that the whole run takes about a minute).
 
 Multi-GPU: the transform of one image does not shard, so N GPUs run N
 independent replicas (weak scaling); value = pixels of all ranks / max time.
@@ -47,7 +48,7 @@ UNIT = "Gpixel/s"
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--size", type=int, default=8192)
@@ -122,7 +123,7 @@ class ClockSampler:
     def start(self):
         try:
             self.proc = subprocess.Popen(
-                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "50",
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "20",
                  "-i", self.gpu_id], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             threading.Thread(target=self._read, daemon=True).start()
         except OSError:
@@ -154,6 +155,23 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(inside)}
 
 
+def max_over_ranks(value, world, device):
+    """The largest `value` over all ranks (the slowest replica sets the
+    whole-job time); the value itself with one rank."""
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, world, ms_max):
+    """Units of all ranks (replicas do equal work) per second of the slowest."""
+    return world * units_per_rank / (ms_max / 1e3)
+
+
 def cpu_baseline_oracle(a, n=None):
     """The oracle as it stands (single-threaded C, FP64) on host cores."""
     import numpy as np
@@ -171,23 +189,37 @@ def cpu_baseline_oracle(a, n=None):
 
 
 def run_reference(a, rank, world):
+    """The reference arm: the oracle as it stands (plain C, FP64, one thread)
+    timed on the host cores, on rank 0 only.  Each step transforms one
+    square sample of the workload (same recipe, wavelet and levels, forward
+    then inverse); its side is chosen from a quick calibration so that the
+    whole --steps K --warmup W run takes about a minute."""
     if rank != 0:
         return
     import numpy as np
 
     import oracle
     from paper_1605_00561_gb300 import inputs
-    n = 1024
     oid = oracle.CDF97 if a.wavelet == "cdf97" else oracle.CDF53
+    levels = lambda m: min(a.levels, oracle.max_levels(m, m))
+    xc = inputs.textured_image(256, 256, seed=2).astype(np.float64)
+    t = time.perf_counter()
+    oracle.dwt2(oracle.dwt2(xc, oid, levels(256)), oid, levels(256), inverse=True)
+    per_px = (time.perf_counter() - t) / (256 * 256)
+    budget = 60.0 / max(1, a.steps + a.warmup)
+    n = int((budget / per_px) ** 0.5) // 64 * 64
+    n = max(64, min(1024, n))
+    L = levels(n)
     x = inputs.textured_image(n, n, seed=2).astype(np.float64)
     for _ in range(a.warmup):
-        oracle.dwt2(oracle.dwt2(x, oid, a.levels), oid, a.levels, inverse=True)
+        oracle.dwt2(oracle.dwt2(x, oid, L), oid, L, inverse=True)
     t = time.perf_counter()
     for _ in range(a.steps):
-        oracle.dwt2(oracle.dwt2(x, oid, a.levels), oid, a.levels, inverse=True)
+        oracle.dwt2(oracle.dwt2(x, oid, L), oid, L, inverse=True)
     dt = time.perf_counter() - t
     value = 2.0 * n * n * a.steps / dt / 1e9
-    sample = f"{n}x{n} per step (same textured recipe, CDF, levels, fwd+inv), FP64 C oracle, 1 thread"
+    sample = (f"{n}x{n} per step (same textured recipe and wavelet, {L} levels, fwd+inv), FP64 C oracle, "
+              "1 thread")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": a.gpus,
         "steps": a.steps, "warmup": a.warmup, "ms_per_step": dt * 1e3 / a.steps, "higher_is_better": True,
@@ -196,14 +228,6 @@ def run_reference(a, rank, world):
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
-
-
-# ---------------------------------------------------------------------------
-# Other workloads
-# ---------------------------------------------------------------------------
-ALL_SCHEMES = ["rowcol", "sweldens", "iwahashi", "iwahashi*", "explosive", "explosive*", "monolithic",
-               "monolithic*", "polyphase", "polyphase*", "convolution"]
-
 
 def level_sizes(w, h, levels):
     out = []
@@ -263,6 +287,9 @@ def time_back_to_back(torch, fn, k, warm=2):
     return e0.elapsed_time(e1) * 1e3 / k
 
 
+DD_UNSUPPORTED = ("polyphase", "polyphase*", "convolution")
+
+
 def run_sweep(a):
     import torch
 
@@ -272,15 +299,17 @@ def run_sweep(a):
     sizes = [int(x) for x in a.sizes.split(",")]
     flush = L2Flush(torch)
     l2 = flush.l2
-    rows = []
+    rows, tuned = [], {}
     for si, n in enumerate(sizes):
         x = torch.from_numpy(inputs.textured_image(n, n, seed=2 + si)).cuda()
         c = torch.empty_like(x)
         y = torch.empty_like(x)
         resident = 2 * n * n * 4 <= l2
-        for wl in ("cdf53", "cdf97"):
+        for wl in ("cdf53", "cdf97", "dd137"):
             for L in (1, 6):
                 for sc in schemes:
+                    if wl == "dd137" and sc in DD_UNSUPPORTED:
+                        continue
                     plan = dwt.Plan(n, n, wl, L, "f32", scheme=sc)
                     fl = flush if resident else None
                     t_f = time_calls(torch, lambda: plan.forward(x, c), a.reps, fl)
@@ -293,6 +322,11 @@ def run_sweep(a):
                         rows.append({"size": n, "wavelet": wl, "levels": L, "dir": d, "scheme": sc, "us": t,
                                      "gpx_s": n * n / t / 1e3, "hbm_frac": ab / (t * 1e-6) / 1e9 / peak,
                                      "l2": "flushed" if resident else "larger than L2"})
+                # the autotuner's choice for this configuration
+                plan = dwt.Plan(n, n, wl, L, "f32")
+                dwt.dwt_plan_autotune(plan.handle)
+                tuned[(n, wl, L)] = (plan.scheme, dwt.dwt_plan_get_tile(plan.handle))
+                plan.close()
         del x, c, y
         torch.cuda.empty_cache()
     best = {}
@@ -302,17 +336,23 @@ def run_sweep(a):
             best[k] = r
     if a.out:
         with open(a.out, "w") as f:
-            f.write("| size | wavelet | L | dir | " + " | ".join(schemes) + " | best |\n")
-            f.write("|---" * (5 + len(schemes)) + "|\n")
+            f.write("| size | wavelet | L | dir | " + " | ".join(schemes) + " | best | autotuner (fwd) |\n")
+            f.write("|---" * (6 + len(schemes)) + "|\n")
             for k in sorted(best):
                 cells = []
                 for sc in schemes:
-                    r = next(r for r in rows if (r["size"], r["wavelet"], r["levels"], r["dir"], r["scheme"]) == k + (sc,))
-                    cells.append(f"{r['us']:.1f} us / {r['hbm_frac']:.2f}")
-                f.write(f"| {k[0]} | {k[1]} | {k[2]} | {k[3]} | " + " | ".join(cells) + f" | {best[k]['scheme']} |\n")
+                    r = next((r for r in rows
+                              if (r["size"], r["wavelet"], r["levels"], r["dir"], r["scheme"]) == k + (sc,)), None)
+                    cells.append(f"{r['us']:.1f} us / {r['hbm_frac']:.2f}" if r else "-")
+                sch, (tr, ts) = tuned[k[:3]]
+                f.write(f"| {k[0]} | {k[1]} | {k[2]} | {k[3]} | " + " | ".join(cells) +
+                        f" | {best[k]['scheme']} | {sch}, {tr} rows, {ts} stages |\n")
     print(json.dumps({"mode": "sweep", "unit": "us per transform; hbm_frac of measured copy bandwidth",
                       "peak_gbs": peak, "rows": rows,
-                      "best": {f"{k[0]}/{k[1]}/L{k[2]}/{k[3]}": v["scheme"] for k, v in sorted(best.items())}}),
+                      "best": {f"{k[0]}/{k[1]}/L{k[2]}/{k[3]}": v["scheme"] for k, v in sorted(best.items())},
+                      "autotuned": {f"{k[0]}/{k[1]}/L{k[2]}": {"scheme": v[0], "strip_rows": v[1][0],
+                                                              "stages": v[1][1]}
+                                    for k, v in sorted(tuned.items())}}),
           flush=True)
 
 
@@ -560,13 +600,9 @@ def main():
     sampler.mark("t1")
     barrier()
     clocks = sampler.stop()
-    ms = e0.elapsed_time(e1)
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(e0.elapsed_time(e1), world, "cuda")
     ms_per_step = ms / a.steps
-    value = world * 2.0 * n * n * a.steps / (ms / 1e3) / 1e9
+    value = whole_job_rate(2.0 * n * n * a.steps, world, ms) / 1e9
     assert dwt.dwt_plan_device_status(plan.handle) == dwt.DWT_OK
 
     # Per-kernel durations: the same K steps again with CUDA events around
@@ -620,12 +656,8 @@ def main():
         dwt.dwt2_inverse_host(plan.handle, ch.data_ptr(), pitch, yh.data_ptr(), pitch, sid)
     e1.record(stream)
     torch.cuda.synchronize()
-    ms2 = e0.elapsed_time(e1)
-    if world > 1:
-        t = torch.tensor([ms2], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms2 = float(t.item())
-    e2e = {"value": world * 2.0 * n * n * k2 / (ms2 / 1e3) / 1e9, "unit": UNIT,
+    ms2 = max_over_ranks(e0.elapsed_time(e1), world, "cuda")
+    e2e = {"value": whole_job_rate(2.0 * n * n * k2, world, ms2) / 1e9, "unit": UNIT,
            "h2d_bytes_per_step": 2 * n * n * 4, "d2h_bytes_per_step": 2 * n * n * 4}
 
     cpu = None

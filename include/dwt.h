@@ -113,6 +113,11 @@ dwt_status dwt_plan_set_scheme(dwt_plan plan, dwt_scheme scheme);
  * of range. */
 dwt_status dwt_plan_set_tile(dwt_plan plan, int strip_rows, int stages);
 
+/* The tile the plan's calls use: set by dwt_plan_set_tile, else the
+ * autotuner's choice for this plan (from dwt_plan_autotune or the cache
+ * file), else the defaults.  Either pointer may be NULL. */
+dwt_status dwt_plan_get_tile(dwt_plan plan, int* strip_rows, int* stages);
+
 /* The scheme a call will actually run (DWT_AUTO resolved). */
 dwt_status dwt_plan_get_scheme(dwt_plan plan, dwt_scheme* scheme);
 
@@ -212,9 +217,15 @@ typedef struct {
 dwt_status dwt_plan_set_profiling(dwt_plan plan, int enable);
 dwt_status dwt_plan_read_profile(dwt_plan plan, dwt_kernel_stat* stats, int capacity, int* count);
 
-/* Run the autotuner for this plan now (device memory for a trial image is
- * allocated and freed), persisting the choice to the cache file named by
- * the environment variable DWT_AUTOTUNE_CACHE (if set). */
+/* Run the autotuner for this plan now: time the forward transform of a
+ * trial image (device memory allocated and freed here) for every scheme the
+ * plan's wavelet and dtype support, then the strip height (6..24 rows) and
+ * the ring depth (1..4 stages) for the fastest scheme.  The choice applies
+ * to this plan (the scheme if it is DWT_AUTO, the tile unless the caller set
+ * one) and is appended to the cache file named by the environment variable
+ * DWT_AUTOTUNE_CACHE (if set), which later plans of the same GPU, size,
+ * wavelet, dtype and level count read.  The halo width follows from the
+ * scheme and wavelet. */
 dwt_status dwt_plan_autotune(dwt_plan plan, dwt_stream stream);
 
 dwt_status dwt_plan_destroy(dwt_plan plan);

@@ -365,6 +365,8 @@ struct dwt_plan_s {
   std::vector<cudaEvent_t> pool;
   int nstages = kDefaultStages;
   int strip_rows = kDefaultStripRows;
+  bool tile_set = false;  // the caller chose the tile: the autotuner's choice does not apply
+  bool tuned = false;     // the autotuner cache was consulted
   std::mutex mu;
 };
 
@@ -395,27 +397,34 @@ std::string cache_key(const dwt_plan_s* p) {
   return buf;
 }
 
-int cache_lookup(const std::string& key) {
+// One autotuner choice: scheme and tile (strip rows, ring stages).
+struct Tuned {
+  int scheme = -1, rows = 0, stages = 0;
+};
+
+Tuned cache_lookup(const std::string& key) {
+  Tuned t;
   const char* path = std::getenv("DWT_AUTOTUNE_CACHE");
-  if (!path) return -1;
+  if (!path) return t;
   std::lock_guard<std::mutex> lk(g_cache_mu);
   FILE* f = std::fopen(path, "r");
-  if (!f) return -1;
-  char k[256];
-  int v, found = -1;
-  while (std::fscanf(f, "%255s %d", k, &v) == 2)
-    if (key == k) found = v;
+  if (!f) return t;
+  char line[512], k[256];
+  while (std::fgets(line, sizeof line, f)) {
+    Tuned v;
+    if (std::sscanf(line, "%255s %d %d %d", k, &v.scheme, &v.rows, &v.stages) >= 2 && key == k) t = v;
+  }
   std::fclose(f);
-  return found;
+  return t;
 }
 
-void cache_store(const std::string& key, int scheme) {
+void cache_store(const std::string& key, const Tuned& t) {
   const char* path = std::getenv("DWT_AUTOTUNE_CACHE");
   if (!path) return;
   std::lock_guard<std::mutex> lk(g_cache_mu);
   FILE* f = std::fopen(path, "a");
   if (!f) return;
-  std::fprintf(f, "%s %d\n", key.c_str(), scheme);
+  std::fprintf(f, "%s %d %d %d\n", key.c_str(), t.scheme, t.rows, t.stages);
   std::fclose(f);
 }
 
@@ -434,13 +443,23 @@ bool scheme_supported(int wavelet, int dtype, int scheme) {
   return true;
 }
 
-int resolve_scheme(dwt_plan_s* p) {
-  if (p->scheme != DWT_AUTO) return p->scheme;
-  if (p->auto_scheme < 0) {
-    int s = cache_lookup(cache_key(p));
-    p->auto_scheme = scheme_supported(p->wavelet, p->dtype, s) ? s : default_scheme(p);
+// Applies a cached autotuner choice once per plan: the scheme when the
+// caller left it to DWT_AUTO, the tile when the caller did not set one.
+void apply_cache(dwt_plan_s* p) {
+  if (p->tuned) return;
+  p->tuned = true;
+  const Tuned t = cache_lookup(cache_key(p));
+  if (p->auto_scheme < 0)
+    p->auto_scheme = scheme_supported(p->wavelet, p->dtype, t.scheme) ? t.scheme : default_scheme(p);
+  if (!p->tile_set && t.rows > 0 && t.stages >= 1 && t.stages <= kMaxStages) {
+    p->strip_rows = t.rows;
+    p->nstages = t.stages;
   }
-  return p->auto_scheme;
+}
+
+int resolve_scheme(dwt_plan_s* p) {
+  apply_cache(p);
+  return p->scheme != DWT_AUTO ? p->scheme : p->auto_scheme;
 }
 
 bool device_pointer_ok(const void* ptr, size_t extent, int device) {
@@ -1301,6 +1320,16 @@ dwt_status dwt_plan_set_tile(dwt_plan p, int strip_rows, int stages) {
   std::lock_guard<std::mutex> lk(p->mu);
   p->strip_rows = strip_rows ? strip_rows : kDefaultStripRows;
   p->nstages = stages ? stages : kDefaultStages;
+  p->tile_set = strip_rows != 0 || stages != 0;
+  return DWT_OK;
+}
+
+dwt_status dwt_plan_get_tile(dwt_plan p, int* strip_rows, int* stages) {
+  if (!p) return DWT_EINVAL;
+  std::lock_guard<std::mutex> lk(p->mu);
+  apply_cache(p);
+  if (strip_rows) *strip_rows = p->strip_rows;
+  if (stages) *stages = p->nstages;
   return DWT_OK;
 }
 
@@ -1433,6 +1462,7 @@ dwt_status dwt_plan_autotune(dwt_plan p, dwt_stream stream) {
   if (!p) return DWT_EINVAL;
   std::lock_guard<std::mutex> lk(p->mu);
   if (p->levels == 0) return DWT_OK;
+  DeviceGuard g(p->device);
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   const size_t pitch = round_up((size_t)p->w * p->es, 128);
   void *in = nullptr, *out = nullptr;
@@ -1442,41 +1472,80 @@ dwt_status dwt_plan_autotune(dwt_plan p, dwt_stream stream) {
   cudaEvent_t a = nullptr, b = nullptr;
   if (e == cudaSuccess) e = cudaEventCreate(&a);
   if (e == cudaSuccess) e = cudaEventCreate(&b);
-  int best = -1;
-  float best_ms = 0.f;
-  const int saved = p->scheme;
+  apply_cache(p);
+  const int saved_scheme = p->scheme, saved_rows = p->strip_rows, saved_stages = p->nstages;
   const bool saved_prof = p->profiling;
   p->profiling = false;
+  // best of three timed forward transforms (after two warm-up runs)
+  auto time_it = [&](float* best) {
+    float t = 1e30f;
+    for (int rep = 0; rep < 5; ++rep) {
+      cudaEventRecord(a, s);
+      if (run(p, false, in, pitch, out, pitch, s) != DWT_OK) return false;
+      cudaEventRecord(b, s);
+      if (cudaEventSynchronize(b) != cudaSuccess) return false;
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, a, b);
+      if (rep >= 2) t = std::min(t, ms);
+    }
+    *best = t;
+    return true;
+  };
+  // 1. the scheme, at the default tile
+  Tuned best;
+  float best_ms = 0.f;
+  p->strip_rows = kDefaultStripRows;
+  p->nstages = kDefaultStages;
   for (int sc = DWT_ROWCOL; e == cudaSuccess && sc < NUM_SCHEMES; ++sc) {
     if (!scheme_supported(p->wavelet, p->dtype, sc)) continue;
     p->scheme = sc;
     if (sc == DWT_ROWCOL && ensure_tmp(p) != DWT_OK) continue;
-    float t = 1e30f;
-    bool ok = true;
-    for (int rep = 0; rep < 5 && ok; ++rep) {
-      cudaEventRecord(a, s);
-      ok = run(p, false, in, pitch, out, pitch, s) == DWT_OK;
-      cudaEventRecord(b, s);
-      if (ok && cudaEventSynchronize(b) == cudaSuccess) {
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, a, b);
-        if (rep >= 2) t = std::min(t, ms);
-      }
-    }
-    if (ok && (best < 0 || t < best_ms)) {
-      best = sc;
+    float t;
+    if (time_it(&t) && (best.scheme < 0 || t < best_ms)) {
+      best.scheme = sc;
       best_ms = t;
     }
   }
-  p->scheme = saved;
+  // 2. the strip height of that scheme, then the ring depth
+  best.rows = kDefaultStripRows;
+  best.stages = kDefaultStages;
+  if (best.scheme >= 0) {
+    p->scheme = best.scheme;
+    for (int rows : {6, 8, 12, 16, 24}) {
+      p->strip_rows = rows;
+      float t;
+      if (time_it(&t) && t < best_ms) {
+        best.rows = rows;
+        best_ms = t;
+      }
+    }
+    p->strip_rows = best.rows;
+    for (int st = 1; st <= kMaxStages; ++st) {
+      if (st == kDefaultStages) continue;
+      p->nstages = st;
+      float t;
+      if (time_it(&t) && t < best_ms) {
+        best.stages = st;
+        best_ms = t;
+      }
+    }
+  }
+  p->scheme = saved_scheme;
   p->profiling = saved_prof;
+  if (p->tile_set) {
+    p->strip_rows = saved_rows;
+    p->nstages = saved_stages;
+  } else {
+    p->strip_rows = best.rows;
+    p->nstages = best.stages;
+  }
   if (a) cudaEventDestroy(a);
   if (b) cudaEventDestroy(b);
   cudaFree(in);
   cudaFree(out);
   if (e != cudaSuccess) return from_cuda(e);
-  if (best < 0) return DWT_EUNSUPPORTED;
-  p->auto_scheme = best;
+  if (best.scheme < 0) return DWT_EUNSUPPORTED;
+  p->auto_scheme = best.scheme;
   cache_store(cache_key(p), best);
   return DWT_OK;
 }

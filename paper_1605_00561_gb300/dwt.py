@@ -17,7 +17,7 @@ __all__ = [
     "DWT_OK", "DWT_EINVAL", "DWT_ENOMEM", "DWT_EUNSUPPORTED", "DWT_ECUDA", "DWT_ETIMEOUT", "DWT_EBUSY",
     "DWT_CDF53", "DWT_CDF97", "DWT_DD137", "DWT_F32", "DWT_F16S", "DWT_I32",
     "SCHEMES", "DWT_NORM_JPEG2000", "DWT_NORM_ZETA",
-    "dwt_plan_create", "dwt_plan_set_scheme", "dwt_plan_set_tile", "dwt_plan_get_scheme", "dwt_plan_set_normalization",
+    "dwt_plan_create", "dwt_plan_set_scheme", "dwt_plan_set_tile", "dwt_plan_get_tile", "dwt_plan_get_scheme", "dwt_plan_set_normalization",
     "dwt2_forward", "dwt2_inverse", "dwt2_forward_noalloc", "dwt2_forward_host", "dwt2_inverse_host", "dwt_batch_submit",
     "dwt_plan_device_status", "dwt_plan_set_profiling", "dwt_plan_read_profile", "dwt_plan_autotune",
     "dwt_plan_destroy", "dwt_status_string", "dwt_version", "Plan", "DwtRequest",
@@ -60,6 +60,8 @@ EXPORTS = {
     "dwt_plan_set_scheme": ([ctypes.c_void_p, ctypes.c_int], ctypes.c_int),
     "dwt_plan_get_scheme": ([ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
     "dwt_plan_set_tile": ([ctypes.c_void_p, ctypes.c_int, ctypes.c_int], ctypes.c_int),
+    "dwt_plan_get_tile": ([ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)],
+                          ctypes.c_int),
     "dwt_plan_set_normalization": ([ctypes.c_void_p, ctypes.c_int], ctypes.c_int),
     "dwt2_forward": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_size_t,
                       ctypes.c_void_p], ctypes.c_int),
@@ -127,6 +129,13 @@ def dwt_plan_set_scheme(plan: int, scheme: int) -> None:
 
 def dwt_plan_set_tile(plan: int, strip_rows: int = 0, stages: int = 0) -> None:
     _check(lib().dwt_plan_set_tile(plan, strip_rows, stages), "dwt_plan_set_tile")
+
+
+def dwt_plan_get_tile(plan: int):
+    """(strip_rows, stages) the plan's calls use."""
+    r, st = ctypes.c_int(), ctypes.c_int()
+    _check(lib().dwt_plan_get_tile(plan, ctypes.byref(r), ctypes.byref(st)), "dwt_plan_get_tile")
+    return r.value, st.value
 
 
 def dwt_plan_get_scheme(plan: int) -> int:

@@ -160,9 +160,17 @@ class Server:
         self._next_stream = (self._next_stream + 1) % len(self.streams)
         with torch.cuda.stream(stream):
             status = torch.empty(len(reqs), dtype=torch.int32, device=self.device)
-            entries = []
+            # every output of the batch is a view of one allocation (256-byte
+            # aligned offsets): one allocator call per batch, not per request
+            offs, total = [], 0
             for r in reqs:
-                r.out = torch.empty((r.h, r.w), dtype=TDT[r.dtype], device=self.device)
+                offs.append(total)
+                total += (r.w * r.h * ELEM[r.dtype] + 255) // 256 * 256
+            slab = torch.empty(max(total, 256), dtype=torch.uint8, device=self.device)
+            entries = []
+            for r, off in zip(reqs, offs):
+                n = r.w * r.h * ELEM[r.dtype]
+                r.out = slab[off:off + n].view(TDT[r.dtype]).view(r.h, r.w)
                 entries.append(self._plan(r).request(r.src, r.out, r.inverse))
             dwt.submit(entries, status=status, stream=stream.cuda_stream)
             # read back on the batch's own stream: no synchronisation with

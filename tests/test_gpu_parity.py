@@ -248,3 +248,31 @@ def test_profiling_reports_every_level(dwt):
     assert prof[0]["algorithmic_bytes"] == 2 * 256 * 256 * 4
     assert all(p["total_ms"] > 0 for p in prof)
     plan.close()
+
+
+def test_autotune_scheme_and_tile_cached(dwt, tmp_path, monkeypatch):
+    monkeypatch.setenv("DWT_AUTOTUNE_CACHE", str(tmp_path / "tune.txt"))
+    h, w, L = 700, 1000, 3
+    p = dwt.Plan(w, h, "cdf97", L, "f32")
+    dwt.dwt_plan_autotune(p.handle)
+    scheme = p.scheme
+    rows, stages = dwt.dwt_plan_get_tile(p.handle)
+    assert scheme in FLOAT_SCHEMES
+    assert rows in (6, 8, 10, 12, 16, 24) and 1 <= stages <= 4
+    # the tuned plan still computes the transform
+    x = inputs.uniform_image(h, w, seed=77)
+    ref = oracle.dwt2(x.astype(np.float64), oracle.CDF97, L)
+    xd = torch.from_numpy(x).cuda()
+    c = torch.empty_like(xd)
+    p.forward(xd, c)
+    torch.cuda.synchronize()
+    assert np.abs(c.cpu().numpy() - ref).max() <= TOL_F32
+    # a new plan of the same shape takes the cached choice
+    q = dwt.Plan(w, h, "cdf97", L, "f32")
+    assert q.scheme == scheme and dwt.dwt_plan_get_tile(q.handle) == (rows, stages)
+    # a tile set by the caller wins over the cache
+    r = dwt.Plan(w, h, "cdf97", L, "f32")
+    dwt.dwt_plan_set_tile(r.handle, 8, 3)
+    assert dwt.dwt_plan_get_tile(r.handle) == (8, 3)
+    for plan in (p, q, r):
+        plan.close()
