@@ -54,7 +54,6 @@ constexpr int kStageStride =
                cmax_bytes(cmax_bytes(K4::STAGE_BYTES, K5::STAGE_BYTES),
                           cmax_bytes(cmax_bytes(K6::STAGE_BYTES, K7::STAGE_BYTES),
                                      cmax_bytes(K8::STAGE_BYTES, K9::STAGE_BYTES))));
-constexpr uint32_t kDepSpins = 1u << 22;  // x ~0.1-1 us of nanosleep: seconds at most
 
 __constant__ ConvTaps kNoTaps;  // none of the batch kinds reads taps
 
@@ -97,12 +96,6 @@ __device__ __forceinline__ bool dispatch(const BatchLevel& L, int cs, int rs, bo
   return false;
 }
 
-__device__ __forceinline__ int load_acquire(const int* p) {
-  int v;
-  asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-
 // 12 resident one-warp blocks per SM leave 168 registers a thread: the
 // strip functions of the kinds (not inlined, each with its own allocation)
 // fit with at most a few bytes of spill in the rarely used ones.
@@ -132,38 +125,13 @@ __global__ void __launch_bounds__(32, 12) batch_kernel(const __grid_constant__ B
     const int rs = item.strip / L.a.ncs, cs = item.strip - rs * L.a.ncs;
     bool ok = true;
     if (L.dep_row_base >= 0) {
-      // lane i watches dependency row lo + i (+ 32, ...): each lane acquires
-      // the writes of the strips it watched, and the warp barrier below
-      // passes them on to the lanes that read the data
       const int2 d = P.row_deps[L.row_base + rs];
-      const int need = L.dep_ncs;
-      for (int r0 = d.x; r0 <= d.y && ok; r0 += 32) {
-        const int r = r0 + lane;
-        bool mine = r > d.y;
-        for (uint32_t spins = 0;; ++spins) {
-          if (!mine) mine = load_acquire(&P.row_done[L.dep_row_base + r]) >= need;
-          if (__all_sync(kFull, mine)) break;
-          if (spins >= kDepSpins) {
-            ok = false;
-            break;
-          }
-          __nanosleep(64);
-        }
-      }
-      __syncwarp();
-      // the awaited strips were written through the generic proxy; this
-      // warp reads them by TMA (async proxy) as well
-      ptx::fence_proxy_async_global();
+      ok = wait_rows(P.row_done + L.dep_row_base, d.x, d.y, L.dep_ncs);
     }
     if (ok) ok = dispatch(L, cs, rs, item.level != fenced, smem_raw, bars, chunk_ctr);
     fenced = item.level;
     if (!ok && lane == 0) atomicExch(&P.req_status[L.request], 5 /* DWT_ETIMEOUT */);
-    // publish this strip: the warp's stores, then one release by lane 0
-    __syncwarp();
-    if (lane == 0) {
-      __threadfence();
-      atomicAdd(&P.row_done[L.row_base + rs], 1);
-    }
+    publish_row(P.row_done + L.row_base, rs);
     it = __shfl_sync(kFull, next, 0);
   }
 }

@@ -350,8 +350,10 @@ struct dwt_plan_s {
   int device = 0;
   size_t es = 4;
   std::vector<int> W, H;
-  void* scratch[2] = {nullptr, nullptr};
-  size_t scratch_pitch = 0;
+  // LL_k of every level but the last, each in its own buffer
+  std::vector<void*> ll;
+  std::vector<size_t> ll_pitch;
+
   void* tmp = nullptr;
   size_t tmp_pitch = 0;
   void* stage_in = nullptr;
@@ -512,10 +514,16 @@ int slot_of(dwt_plan_s* p, const std::string& name) {
   return (int)p->slots.size() - 1;
 }
 
-// One launch: geometry, descriptors, optional timing events.
-dwt_status launch(dwt_plan_s* p, const LaunchKey& key, LevelArgs& a, const Coefs& cf,
-                  const ConvTaps& ct, cudaStream_t s, const char* slot) {
-  KernelInfo ki{};
+// Dynamic shared memory of a level kernel with `nstages` ring stages, from
+// its info for `info_stages` stages.
+size_t smem_with_stages(const KernelInfo& ki, int info_stages, int nstages) {
+  const size_t bars = (size_t)kWarpsPerCta * kMaxStages * 8;
+  return (ki.smem_bytes - bars) / info_stages * nstages + bars;
+}
+
+// Strips of one level: column strips, strip height, strip rows and ring
+// depth, for the kernel of `key`.
+dwt_status level_geometry(const dwt_plan_s* p, const LaunchKey& key, LevelArgs& a, KernelInfo& ki) {
   if (!find_kernel(key, p->nstages, &ki)) return DWT_EUNSUPPORTED;
   const Occ oc = occupancy(ki, p->device);
   const int cap = oc.sms * oc.per_sm;
@@ -529,10 +537,18 @@ dwt_status launch(dwt_plan_s* p, const LaunchKey& key, LevelArgs& a, const Coefs
   // as the level still fits one wave with the larger shared-memory ring
   a.nstages = p->nstages;
   if (p->nstages < kMaxStages && (long long)a.ncs * a.nrs < cap) {
-    const size_t stage = (ki.smem_bytes - (size_t)kWarpsPerCta * kMaxStages * 8) / p->nstages;
-    const Occ deep = occupancy(ki.fn, stage * kMaxStages + (size_t)kWarpsPerCta * kMaxStages * 8, p->device);
+    const Occ deep = occupancy(ki.fn, smem_with_stages(ki, p->nstages, kMaxStages), p->device);
     if ((long long)a.ncs * a.nrs <= (long long)deep.sms * deep.per_sm) a.nstages = kMaxStages;
   }
+  return DWT_OK;
+}
+
+// One launch: geometry, descriptors, optional timing events.
+dwt_status launch(dwt_plan_s* p, const LaunchKey& key, LevelArgs& a, const Coefs& cf,
+                  const ConvTaps& ct, cudaStream_t s, const char* slot) {
+  KernelInfo ki{};
+  const dwt_status g = level_geometry(p, key, a, ki);
+  if (g != DWT_OK) return g;
   a.status = p->d_status;
 
   TmaMaps maps;
@@ -585,13 +601,55 @@ dwt_status ensure_tmp(dwt_plan_s* p) {
   return from_cuda(cudaMalloc(&p->tmp, p->tmp_pitch * p->h));
 }
 
+// Which strip rows of level d (the level whose output level a reads) each
+// strip row of level a needs: the rows its chunks load (the strip plus
+// halo, padded to whole chunks), mirrored the way the kernel mirrors them,
+// mapped to the strip rows of d that write them.  In-range rows map
+// monotonically (their span is exact); only the few halo rows beyond an
+// edge are mirrored one by one.  out[rs] = (first, last) for every rs < a.nrs.
+void row_dependencies(const LevelArgs& a, const LevelArgs& d, const KernelInfo& ki, bool inverse, int2* out) {
+  const int CH = chunk_rows(ki);
+  // forward: sample rows of the level = LL quad rows of the level before,
+  // written by its strip row y / T; inverse: LL plane rows = sample rows
+  // of the coarser level's output, written by its strip row y / (2 T)
+  const int n = inverse ? a.ch : a.H;
+  const int per = inverse ? 2 * d.T : d.T;
+  auto row_of = [&](int y) {
+    int ym;
+    if (inverse) ym = a.H == 1 ? 0 : (y >= 0 && y < a.ch) ? y : (host_mirror(2 * y, a.H) >> 1);
+    else ym = a.H == 1 ? 0 : host_mirror(y, a.H);
+    return ym / per;
+  };
+  for (int rs = 0; rs < a.nrs; ++rs) {
+    const int q0 = rs * a.T;
+    const int rows_out = std::min(a.T, a.ch - q0);
+    const int nchunks = (rows_out + ki.up + ki.down + CH - 1) / CH;
+    const int y0 = q0 - ki.up, y1 = y0 + nchunks * CH;                 // quad rows loaded
+    const int r0 = inverse ? y0 : 2 * y0, r1 = inverse ? y1 : 2 * y1;  // rows of the read plane
+    int lo = INT32_MAX, hi = -1;
+    const int in0 = std::max(r0, 0), in1 = std::min(r1, n);
+    if (in0 < in1) {
+      lo = in0 / per;
+      hi = (in1 - 1) / per;
+    }
+    for (int y = r0; y < std::min(r1, 0); ++y) {
+      lo = std::min(lo, row_of(y));
+      hi = std::max(hi, row_of(y));
+    }
+    for (int y = std::max(r0, n); y < r1; ++y) {
+      lo = std::min(lo, row_of(y));
+      hi = std::max(hi, row_of(y));
+    }
+    out[rs] = make_int2(std::max(lo, 0), std::min(hi, d.nrs - 1));
+  }
+}
+
 // Where level k of a transform reads and writes (Mallat layout): the four
 // subband planes inside the coefficient buffer, with LL_k in the buffer
 // ll[k] (pitch llp[k] bytes) except at the coarsest level, and the level's
-// sample plane (the image at level 0, LL_{k-1} above).  Single-image calls
-// pass the plan's ping-pong scratch for every k; batches give each level
-// its own buffer, so that overlapping levels never overwrite data another
-// level still reads.
+// sample plane (the image at level 0, LL_{k-1} above).  Every level has its
+// own LL buffer (about w*h/3 elements in all): in batches the levels of an
+// image overlap, so no level may overwrite data another level still reads.
 struct LevelIO {
   const void* band[4];
   long long bpitch[4];
@@ -646,7 +704,7 @@ void fused_io(const LevelIO& io, bool inverse, LevelArgs& a) {
   }
 }
 
-// A plan's own device memory (status word, LL ping-pong scratch), made on
+// A plan's own device memory (status word, one LL buffer per level), made on
 // its first single-image call: plans used only in batches never allocate.
 dwt_status ensure_device(dwt_plan_s* p) {
   cudaError_t e = cudaSuccess;
@@ -659,18 +717,20 @@ dwt_status ensure_device(dwt_plan_s* p) {
       return from_cuda(e);
     }
   }
-  if (p->levels >= 2 && !p->scratch[0]) {
-    p->scratch_pitch = round_up((size_t)p->W[1] * p->es, 128);
-    void *s0 = nullptr, *s1 = nullptr;
-    e = cudaMalloc(&s0, p->scratch_pitch * p->H[1]);
-    if (e == cudaSuccess) e = cudaMalloc(&s1, p->scratch_pitch * p->H[2]);
-    if (e != cudaSuccess) {
-      cudaFree(s0);
-      cudaFree(s1);
-      return from_cuda(e);
+  if (p->levels >= 2 && p->ll.empty()) {
+    for (int k = 0; k + 1 < p->levels; ++k) {
+      const size_t pitch = round_up((size_t)p->W[k + 1] * p->es, 128);
+      void* q = nullptr;
+      e = cudaMalloc(&q, pitch * p->H[k + 1]);
+      if (e != cudaSuccess) {
+        for (void* r : p->ll) cudaFree(r);
+        p->ll.clear();
+        p->ll_pitch.clear();
+        return from_cuda(e);
+      }
+      p->ll.push_back(q);
+      p->ll_pitch.push_back(pitch);
     }
-    p->scratch[0] = s0;
-    p->scratch[1] = s1;
   }
   return DWT_OK;
 }
@@ -713,10 +773,11 @@ dwt_status run(dwt_plan_s* p, bool inverse, const void* src, size_t src_pitch, v
   const Lifting L = lifting_of(p->wavelet);
   const int Lv = p->levels;
   char slot[32];
-  // LL ping-pong: LL_k in scratch[k & 1]
-  std::vector<void*> ll(Lv);
-  std::vector<size_t> llp(Lv, p->scratch_pitch);
-  for (int k = 0; k < Lv; ++k) ll[k] = p->scratch[k & 1];
+  std::vector<void*> ll(p->ll);
+  std::vector<size_t> llp(p->ll_pitch);
+  ll.resize(Lv, nullptr);
+  llp.resize(Lv, 0);
+
   for (int step = 0; step < Lv; ++step) {
     const int k = inverse ? Lv - 1 - step : step;
     LevelArgs a{};
@@ -930,53 +991,12 @@ dwt_status batch_submit(const dwt_request* reqs, int n, cudaStream_t s, int* d_s
   }
   const int nl = (int)levels.size();
 
-  // which strip rows of the level it reads each strip row needs: the rows
-  // its chunks load (strip plus halo, padded to whole chunks), mirrored
-  // the way the kernel mirrors them, mapped to the strip rows that write
-  // them.  In-range rows map monotonically (their span is exact); only the
-  // few halo rows beyond an edge are mirrored one by one.
   std::vector<int2> row_deps(nrows, make_int2(0, -1));
   for (int l = 0; l < nl; ++l) {
     const BatchLevel& bl = levels[l];
     if (bl.dep_row_base < 0) continue;
-    const BatchLevel& dl = levels[l - 1];
-    const KernelInfo& ki = kinfo[bl.kind];
-    const bool inverse = reqs[bl.request].inverse != 0;
-    const LevelArgs& a = bl.a;
-    const int CH = ki.load == SAMPLES ? ki.box_h / 2 : ki.box_h;
-    // forward: sample rows of the level = LL quad rows of the level before,
-    // written by its strip row y / T; inverse: LL plane rows = sample rows
-    // of the coarser level's output, written by its strip row y / (2 T)
-    const int n = inverse ? a.ch : a.H;
-    const int per = inverse ? 2 * dl.a.T : dl.a.T;
-    auto row_of = [&](int y) {
-      int ym;
-      if (inverse) ym = a.H == 1 ? 0 : (y >= 0 && y < a.ch) ? y : (host_mirror(2 * y, a.H) >> 1);
-      else ym = a.H == 1 ? 0 : host_mirror(y, a.H);
-      return ym / per;
-    };
-    for (int rs = 0; rs < a.nrs; ++rs) {
-      const int q0 = rs * a.T;
-      const int rows_out = std::min(a.T, a.ch - q0);
-      const int nchunks = (rows_out + ki.up + ki.down + CH - 1) / CH;
-      const int y0 = q0 - ki.up, y1 = y0 + nchunks * CH;  // quad rows loaded
-      const int r0 = inverse ? y0 : 2 * y0, r1 = inverse ? y1 : 2 * y1;  // rows of the read plane
-      int lo = INT32_MAX, hi = -1;
-      const int in0 = std::max(r0, 0), in1 = std::min(r1, n);
-      if (in0 < in1) {
-        lo = in0 / per;
-        hi = (in1 - 1) / per;
-      }
-      for (int y = r0; y < std::min(r1, 0); ++y) {
-        lo = std::min(lo, row_of(y));
-        hi = std::max(hi, row_of(y));
-      }
-      for (int y = std::max(r0, n); y < r1; ++y) {
-        lo = std::min(lo, row_of(y));
-        hi = std::max(hi, row_of(y));
-      }
-      row_deps[bl.row_base + rs] = make_int2(std::max(lo, 0), std::min(hi, dl.a.nrs - 1));
-    }
+    row_dependencies(bl.a, levels[l - 1].a, kinfo[bl.kind], reqs[bl.request].inverse != 0,
+                     row_deps.data() + bl.row_base);
   }
 
   // queue order: a wavefront.  The first level of each request enters in
@@ -1556,10 +1576,10 @@ dwt_status dwt_plan_destroy(dwt_plan p) {
     DeviceGuard g(p->device);
     // plans used only in batches own no device memory and nothing on the
     // device refers to them: no synchronisation
-    const bool owns = p->scratch[0] || p->scratch[1] || p->tmp || p->stage_in || p->stage_out || p->d_status;
+    const bool owns = !p->ll.empty() || p->tmp || p->stage_in || p->stage_out || p->d_status;
     if (owns && (p->last_stream || !p->pending.empty())) cudaDeviceSynchronize();
-    for (void* q : {p->scratch[0], p->scratch[1], p->tmp, p->stage_in, p->stage_out,
-                    static_cast<void*>(p->d_status)})
+    for (void* q : p->ll) cudaFree(q);
+    for (void* q : {p->tmp, p->stage_in, p->stage_out, static_cast<void*>(p->d_status)})
       if (q) cudaFree(q);
     for (const ProfRec& r : p->pending) {
       cudaEventDestroy(r.a);

@@ -606,6 +606,52 @@ __device__ __forceinline__ void strip_coords(int s, int ncs, int nrs, int& cs, i
   }
 }
 
+// Waits, bounded, until the completion counters dep[lo..hi] all reach
+// `need`.  Lane i watches rows lo + i, lo + i + 32, ...; each lane acquires
+// the writes of the strips it watched, and the warp barrier at the end
+// passes them on to the lanes that read the data.  Returns false if the
+// wait ran out.
+constexpr uint32_t kDepSpins = 1u << 22;  // x ~0.1-1 us of nanosleep: seconds at most
+
+__device__ __forceinline__ int load_acquire(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ bool wait_rows(const int* dep, int lo, int hi, int need) {
+  const int lane = threadIdx.x & 31;
+  bool ok = true;
+  for (int r0 = lo; r0 <= hi && ok; r0 += 32) {
+    const int r = r0 + lane;
+    bool mine = r > hi;
+    for (uint32_t spins = 0;; ++spins) {
+      if (!mine) mine = load_acquire(dep + r) >= need;
+      if (__all_sync(kFull, mine)) break;
+      if (spins >= kDepSpins) {
+        ok = false;
+        break;
+      }
+      __nanosleep(64);
+    }
+  }
+  __syncwarp();
+  // the awaited strips were written through the generic proxy; the warp
+  // reads them by TMA (async proxy) as well
+  ptx::fence_proxy_async_global();
+  return ok;
+}
+
+// Publishes a finished strip of row rs: after the warp barrier (which
+// orders every lane's stores before lane 0's next operation), lane 0 adds
+// one to the row's counter with release semantics.  A reduction returns
+// nothing, so the warp does not wait for it.
+__device__ __forceinline__ void publish_row(int* done, int rs) {
+  __syncwarp();
+  if ((threadIdx.x & 31) == 0)
+    asm volatile("red.release.gpu.global.add.s32 [%0], 1;" ::"l"(done + rs) : "memory");
+}
+
 // Lift strip (cs, rs): column strip cs, quad rows [rs*T, rs*T + T).  `ring`
 // is the warp's shared-memory ring (nstages stages; the stage size the
 // caller reserved is passed as `stage_stride`), `bars` its barriers
@@ -700,12 +746,12 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, C::MIN_WARPS / kWarpsPerCta
     }
   }
   __syncwarp();
+  int cs, rs;
+  strip_coords(strip, a.ncs, a.nrs, cs, rs);
   // the previous level's kernel may still be running: every read and write
   // of level data comes after this point
   ptx::wait_prerequisites();
   uint32_t chunk_ctr = 0;
-  int cs, rs;
-  strip_coords(strip, a.ncs, a.nrs, cs, rs);
   run_strip<C>(a, maps, cf, ct, cs, rs, ring, C::STAGE_BYTES, bars, chunk_ctr);
 }
 
