@@ -30,6 +30,11 @@
  *   - The transform is out-of-place: input and output must not overlap.
  *   - A plan owns its scratch memory; one plan must not be in flight on two
  *     streams at once (use one plan per concurrent slot).
+ *   - Once a plan has made one single-image call (which allocates its device
+ *     memory), its dwt2_forward / dwt2_inverse calls can be captured into a
+ *     CUDA graph by stream capture and replayed; the levels keep their
+ *     programmatic-dependent-launch edges.  dwt_batch_submit cannot be
+ *     captured (it waits on its upload ring).
  *
  * All functions are thread-safe for distinct plans.
  */

@@ -276,3 +276,36 @@ def test_autotune_scheme_and_tile_cached(dwt, tmp_path, monkeypatch):
     assert dwt.dwt_plan_get_tile(r.handle) == (8, 3)
     for plan in (p, q, r):
         plan.close()
+
+
+def test_plan_calls_replay_from_a_cuda_graph(dwt):
+    """After one eager call (which makes the plan's allocations), forward and
+    inverse calls can be captured into a CUDA graph and replayed on new
+    inputs with the eager results."""
+    h, w, L = 523, 611, 4
+    plan = dwt.Plan(w, h, "cdf97", L, "f32", scheme="monolithic*")
+    x = torch.zeros((h, w), device="cuda")
+    c = torch.empty_like(x)
+    y = torch.empty_like(x)
+    plan.forward(x, c)
+    plan.inverse(c, y)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            plan.forward(x, c, stream=s.cuda_stream)
+            plan.inverse(c, y, stream=s.cuda_stream)
+    for seed in (3, 4):
+        x.copy_(torch.from_numpy(inputs.uniform_image(h, w, seed=seed)))
+        g.replay()
+        torch.cuda.synchronize()
+        ce, ye = torch.empty_like(x), torch.empty_like(x)
+        plan.forward(x, ce)
+        plan.inverse(ce, ye)
+        torch.cuda.synchronize()
+        assert torch.equal(c, ce) and torch.equal(y, ye)
+        ref = oracle.dwt2(x.cpu().numpy().astype(np.float64), oracle.CDF97, L)
+        assert np.abs(c.cpu().numpy() - ref).max() <= TOL_F32
+    assert dwt.dwt_plan_device_status(plan.handle) == dwt.DWT_OK
+    plan.close()
