@@ -110,16 +110,11 @@ __global__ void __launch_bounds__(32, 12) batch_kernel(const __grid_constant__ B
   __syncwarp();
   uint32_t chunk_ctr = 0;
   int fenced = -1;  // level whose tensor maps this warp has acquired
-  // the queue is popped one item ahead: the next index is fetched while the
-  // current strip streams.  A warp holding an unstarted item cannot stall
-  // the queue: the smallest unfinished item is always some warp's current
-  // one, and everything it waits for comes before it.
-  int it = 0;
-  if (lane == 0) it = atomicAdd(P.head, 1);
-  it = __shfl_sync(kFull, it, 0);
-  while (it < P.nitems) {
-    int next = 0;
-    if (lane == 0) next = atomicAdd(P.head, 1);
+  for (;;) {
+    int it = 0;
+    if (lane == 0) it = atomicAdd(P.head, 1);
+    it = __shfl_sync(kFull, it, 0);
+    if (it >= P.nitems) break;
     const BatchItem item = P.items[it];
     const BatchLevel& L = P.levels[item.level];
     const int rs = item.strip / L.a.ncs, cs = item.strip - rs * L.a.ncs;
@@ -132,7 +127,6 @@ __global__ void __launch_bounds__(32, 12) batch_kernel(const __grid_constant__ B
     fenced = item.level;
     if (!ok && lane == 0) atomicExch(&P.req_status[L.request], 5 /* DWT_ETIMEOUT */);
     publish_row(P.row_done + L.row_base, rs);
-    it = __shfl_sync(kFull, next, 0);
   }
 }
 
