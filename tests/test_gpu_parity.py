@@ -309,3 +309,59 @@ def test_plan_calls_replay_from_a_cuda_graph(dwt):
         assert np.abs(c.cpu().numpy() - ref).max() <= TOL_F32
     assert dwt.dwt_plan_device_status(plan.handle) == dwt.DWT_OK
     plan.close()
+
+
+def _interior_bands(coef, k, levels, w, h):
+    """(band name, array) of level k of a Mallat-packed array."""
+    cw, ch = w, h
+    for _ in range(k):
+        cw, ch = (cw + 1) // 2, (ch + 1) // 2
+    lw, lh = (cw + 1) // 2, (ch + 1) // 2
+    bands = {"HL": coef[:lh, lw:cw], "LH": coef[lh:ch, :lw], "HH": coef[lh:ch, lw:cw]}
+    if k == levels - 1:
+        bands["LL"] = coef[:lh, :lw]
+    return bands
+
+
+@pytest.mark.parametrize("wavelet", ["cdf97"])
+def test_largest_sweep_size_interior_against_oracle(dwt, wavelet):
+    """16384 x 16384, 6 levels: the oracle cannot transform the whole image
+    in seconds, but a level-k coefficient depends only on image samples
+    within (filter radius) x 2^(k+1) of it.  The oracle runs on a 4096^2
+    crop placed on a 2^6 grid; the GPU coefficients whose support lies
+    inside the crop must match it."""
+    n, L, S = 16384, 6, 4096
+    r0, c0 = 7 * 1024, 5 * 1024  # multiples of 2^L: the crop keeps the polyphase grid
+    g = torch.Generator(device="cuda")
+    g.manual_seed(11)
+    x = torch.randint(0, 256, (n, n), generator=g, device="cuda", dtype=torch.int32).float()
+    c = torch.empty_like(x)
+    plan = dwt.Plan(n, n, wavelet, L, "f32", scheme="monolithic*")
+    plan.forward(x, c)
+    torch.cuda.synchronize()
+    assert dwt.dwt_plan_device_status(plan.handle) == dwt.DWT_OK
+    plan.close()
+    crop = x[r0:r0 + S, c0:c0 + S].cpu().numpy().astype(np.float64)
+    ref = oracle.dwt2(crop, OID[wavelet], L)
+    cg = c.cpu().numpy()
+    del x, c
+    # A level-k coefficient depends on samples within sum_j 4 * 2^j < 4 *
+    # 2^(k+1) of its position (the 9/7 analysis taps reach 4 samples at
+    # every level): under 4 band units of level k.  The crop's own border
+    # (mirrored) moves the crop's coefficients within that distance of its
+    # edge, so 8 band units of margin are safe.
+    margin = 8
+    checked = 0
+    for k in range(L):
+        step = 2 ** (k + 1)
+        gb = _interior_bands(cg, k, L, n, n)
+        rb = _interior_bands(ref, k, L, S, S)
+        br, bc = r0 // step, c0 // step  # crop origin in level-k band units
+        m = S // step
+        for name in rb:
+            got = gb[name][br + margin:br + m - margin, bc + margin:bc + m - margin]
+            exp = rb[name][margin:m - margin, margin:m - margin]
+            assert got.shape == exp.shape and got.size > 0, (k, name)
+            assert np.abs(got - exp).max() <= TOL_F32, (k, name)
+            checked += got.size
+    assert checked > 1_000_000
