@@ -329,6 +329,35 @@ def run_sweep(a):
                 plan.close()
         del x, c, y
         torch.cuda.empty_cache()
+    # reversible integer 5/3 (12-bit samples): the two schemes that keep the
+    # JPEG 2000 step order, at the sweep's sizes from 4096^2 up and at the odd
+    # 5001 x 3333
+    gi = torch.Generator(device="cuda")
+    gi.manual_seed(7)
+    int_shapes = [(n, n) for n in sizes if n >= 4096] + ([(5001, 3333)] if max(sizes) >= 4096 else [])
+    for (w, h) in int_shapes:
+        x = torch.randint(0, 4096, (h, w), generator=gi, device="cuda", dtype=torch.int32)
+        c = torch.empty_like(x)
+        y = torch.empty_like(x)
+        for L in (1, 5):
+            for sc in ("rowcol", "sweldens"):
+                if sc not in schemes:
+                    continue
+                plan = dwt.Plan(w, h, "cdf53", L, "i32", scheme=sc)
+                t_f = time_calls(torch, lambda: plan.forward(x, c), a.reps)
+                t_i = time_calls(torch, lambda: plan.inverse(c, y), a.reps)
+                torch.cuda.synchronize()
+                assert dwt.dwt_plan_device_status(plan.handle) == dwt.DWT_OK
+                assert torch.equal(x, y)  # bit-exact round trip
+                plan.close()
+                ab = sum(2 * 4 * a_ * b_ for a_, b_ in level_sizes(w, h, L))
+                for d, t in (("fwd", t_f), ("inv", t_i)):
+                    rows.append({"size": f"{w}x{h}", "wavelet": "int53", "levels": L, "dir": d, "scheme": sc,
+                                 "us": t, "gpx_s": w * h / t / 1e3, "hbm_frac": ab / (t * 1e-6) / 1e9 / peak,
+                                 "l2": "larger than L2"})
+            tuned[(f"{w}x{h}", "int53", L)] = ("-", (0, 0))
+        del x, c, y
+        torch.cuda.empty_cache()
     best = {}
     for r in rows:
         k = (r["size"], r["wavelet"], r["levels"], r["dir"])
@@ -338,21 +367,22 @@ def run_sweep(a):
         with open(a.out, "w") as f:
             f.write("| size | wavelet | L | dir | " + " | ".join(schemes) + " | best | autotuner (fwd) |\n")
             f.write("|---" * (6 + len(schemes)) + "|\n")
-            for k in sorted(best):
+            for k in sorted(best, key=lambda k: (str(k[0]).zfill(12), k[1], k[2], k[3])):
                 cells = []
                 for sc in schemes:
                     r = next((r for r in rows
                               if (r["size"], r["wavelet"], r["levels"], r["dir"], r["scheme"]) == k + (sc,)), None)
                     cells.append(f"{r['us']:.1f} us / {r['hbm_frac']:.2f}" if r else "-")
                 sch, (tr, ts) = tuned[k[:3]]
+                pick = f"{sch}, {tr} rows, {ts} stages" if tr else "-"
                 f.write(f"| {k[0]} | {k[1]} | {k[2]} | {k[3]} | " + " | ".join(cells) +
-                        f" | {best[k]['scheme']} | {sch}, {tr} rows, {ts} stages |\n")
+                        f" | {best[k]['scheme']} | {pick} |\n")
     print(json.dumps({"mode": "sweep", "unit": "us per transform; hbm_frac of measured copy bandwidth",
                       "peak_gbs": peak, "rows": rows,
-                      "best": {f"{k[0]}/{k[1]}/L{k[2]}/{k[3]}": v["scheme"] for k, v in sorted(best.items())},
+                      "best": {f"{k[0]}/{k[1]}/L{k[2]}/{k[3]}": v["scheme"] for k, v in best.items()},
                       "autotuned": {f"{k[0]}/{k[1]}/L{k[2]}": {"scheme": v[0], "strip_rows": v[1][0],
                                                               "stages": v[1][1]}
-                                    for k, v in sorted(tuned.items())}}),
+                                    for k, v in tuned.items()}}),
           flush=True)
 
 

@@ -10,9 +10,10 @@
  * Convolution) computes the same coefficients up to rounding (Sec. 7).
  *
  * Conventions shared by every entry point:
- *   - Images are row-major 2-D planes with a row pitch in BYTES.  Device
- *     pointers must be CUDA device (or managed) memory; host pointers are
- *     rejected with DWT_EINVAL, never dereferenced on the GPU.
+ *   - Images are row-major 2-D planes with a row pitch in BYTES (a multiple
+ *     of the element size, as are the plane addresses).  Device pointers
+ *     must be CUDA device (or managed) memory; host pointers are rejected
+ *     with DWT_EINVAL, never dereferenced on the GPU.
  *   - Output layout (forward) / input layout (inverse): Mallat packing of a
  *     w x h plane.  At level k the level's input is W_k x H_k (W_0 = w,
  *     W_{k+1} = ceil(W_k / 2)); its LL band is ceil(W_k/2) x ceil(H_k/2) at

@@ -742,6 +742,8 @@ dwt_status check_buffers(const dwt_plan_s* p, const void* src, size_t src_pitch,
   if (src_pitch < (size_t)p->w * es || dst_pitch < (size_t)p->w * es || src_pitch % es ||
       dst_pitch % es)
     return DWT_EINVAL;
+  // samples are accessed whole: the planes must start on an element boundary
+  if (reinterpret_cast<uintptr_t>(src) % es || reinterpret_cast<uintptr_t>(dst) % es) return DWT_EINVAL;
   const size_t nsrc = plane_extent(p->w, p->h, src_pitch, es);
   const size_t ndst = plane_extent(p->w, p->h, dst_pitch, es);
   if (!device_pointer_ok(src, nsrc, p->device) || !device_pointer_ok(dst, ndst, p->device))
@@ -1198,6 +1200,7 @@ dwt_status forward_on_scratch(int w, int h, int wavelet, int levels, int dtype, 
   const size_t es = elem_size(dtype);
   if (src_pitch < (size_t)w * es || dst_pitch < (size_t)w * es || src_pitch % es || dst_pitch % es)
     return DWT_EINVAL;
+  if (reinterpret_cast<uintptr_t>(src) % es || reinterpret_cast<uintptr_t>(dst) % es) return DWT_EINVAL;
   int device = -1;
   if (cudaGetDevice(&device) != cudaSuccess) return DWT_ECUDA;
   const size_t nsrc = plane_extent(w, h, src_pitch, es), ndst = plane_extent(w, h, dst_pitch, es);

@@ -29,6 +29,8 @@
 // of each sample row.
 #pragma once
 
+#include <type_traits>
+
 #include <cuda_fp16.h>
 
 #include "programs.cuh"
@@ -70,6 +72,45 @@ __device__ __forceinline__ void copy_bytes(void* d, const void* s) {
   } else {
     static_assert(N == 4, "unsupported copy size");
     *reinterpret_cast<int*>(d) = *reinterpret_cast<const int*>(s);
+  }
+}
+
+// The bits of a 4-byte sample.
+template <typename T>
+__device__ __forceinline__ int bits32(T x) {
+  if constexpr (sizeof(T) == 4 && !std::is_integral<T>::value) return __float_as_int(x);
+  else return static_cast<int>(x);
+}
+
+// Stores the N 4-byte values v at p, where p lies A elements past a 16-byte
+// boundary, with the widest aligned stores: 4-byte pieces up to an 8-byte
+// boundary, 8-byte pieces up to a 16-byte one, then 16-byte pieces.  The
+// vectors are assembled from the values' bits (no reinterpreted arrays).
+template <int N, int A, typename T>
+__device__ __forceinline__ void store_split(T* p, const T* v) {
+  if constexpr (N > 0) {
+    if constexpr (A == 0 && N >= 4) {
+      *reinterpret_cast<int4*>(p) = make_int4(bits32(v[0]), bits32(v[1]), bits32(v[2]), bits32(v[3]));
+      store_split<N - 4, 0>(p + 4, v + 4);
+    } else if constexpr (A % 2 == 0 && N >= 2) {
+      *reinterpret_cast<int2*>(p) = make_int2(bits32(v[0]), bits32(v[1]));
+      store_split<N - 2, (A + 2) % 4>(p + 2, v + 2);
+    } else {
+      *reinterpret_cast<int*>(p) = bits32(v[0]);
+      store_split<N - 1, (A + 1) % 4>(p + 1, v + 1);
+    }
+  }
+}
+
+// N in-bounds 4-byte values at p, whose offset from a 16-byte boundary is
+// the same in every lane of the warp (lanes store runs 16 or 32 bytes apart).
+template <int N, typename T>
+__device__ __forceinline__ void store_run(T* p, const T* v) {
+  switch ((reinterpret_cast<uintptr_t>(p) >> 2) & 3) {
+    case 0: store_split<N, 0>(p, v); break;
+    case 1: store_split<N, 1>(p, v); break;
+    case 2: store_split<N, 2>(p, v); break;
+    default: store_split<N, 3>(p, v); break;
   }
 }
 
@@ -554,10 +595,12 @@ struct Strip {
         ST v[QL];
 #pragma unroll
         for (int j = 0; j < QL; ++j) v[j] = StoreT<ST>::from_v(r.s[p][j]);
+        const int pw = (p & 1) ? a.fw : a.cw;
         if (o.vec[p]) {
           copy_bytes<QL * C::ES>(rowp, v);
+        } else if (C::ES == 4 && m + QL <= pw) {
+          store_run<QL>(rowp, v);
         } else {
-          const int pw = (p & 1) ? a.fw : a.cw;
 #pragma unroll
           for (int j = 0; j < QL; ++j)
             if (m + j < pw) rowp[j] = v[j];
@@ -579,6 +622,8 @@ struct Strip {
         }
         if (o.vec[0]) {
           copy_bytes<2 * QL * C::ES>(rowp, v);
+        } else if (C::ES == 4 && gx + 2 * QL <= a.W) {
+          store_run<2 * QL>(rowp, v);
         } else {
 #pragma unroll
           for (int t = 0; t < 2 * QL; ++t)

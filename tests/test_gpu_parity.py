@@ -365,3 +365,35 @@ def test_largest_sweep_size_interior_against_oracle(dwt, wavelet):
             assert np.abs(got - exp).max() <= TOL_F32, (k, name)
             checked += got.size
     assert checked > 1_000_000
+
+
+def test_misaligned_base_pointer_rejected(dwt):
+    plan = dwt.Plan(64, 64, "cdf97", 2, "f32")
+    buf = torch.zeros(64 * 64 + 4, device="cuda")
+    out = torch.zeros(64, 64, device="cuda")
+    raw = buf.data_ptr() + 2  # not on a 4-byte boundary
+    with pytest.raises(dwt.DwtError) as e:
+        dwt.dwt2_forward(plan.handle, raw, 256, out.data_ptr(), 256)
+    assert e.value.status == dwt.DWT_EINVAL
+    with pytest.raises(dwt.DwtError) as e:
+        dwt.dwt2_forward(plan.handle, out.data_ptr(), 256, raw, 256)
+    assert e.value.status == dwt.DWT_EINVAL
+    plan.close()
+
+
+@pytest.mark.parametrize("w", [1001, 1002, 1003])
+def test_unaligned_pitches_all_offsets(dwt, w):
+    """Row pitches of 4 w bytes put the rows (and the Mallat bands) at every
+    offset from a 16-byte boundary: the box copies and split stores must
+    agree with the oracle for each."""
+    h, L = 203, 3
+    for wl in ("cdf53", "cdf97"):
+        x = inputs.uniform_image(h, w, seed=w + h)
+        ref = oracle.dwt2(x.astype(np.float64), OID[wl], L)
+        c, y, yo = run_fwd_inv(dwt, x, wl, L, "f32", "monolithic*", coef_in=ref.astype(np.float32))
+        assert np.abs(c - ref).max() <= TOL_F32
+        assert np.abs(yo - x).max() <= TOL_F32
+    xi = inputs.int12_image(h, w, seed=w)
+    refi = oracle.dwt2_int(xi, L)
+    c, y, yo = run_fwd_inv(dwt, xi, "cdf53", L, "i32", "sweldens", coef_in=refi.astype(np.int32))
+    assert np.array_equal(c, refi) and np.array_equal(yo, xi) and np.array_equal(y, xi)
