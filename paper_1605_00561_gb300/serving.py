@@ -40,7 +40,8 @@ TDT = {"f32": torch.float32, "f16s": torch.float16, "i32": torch.int32}
 @dataclass
 class Request:
     """One transform.  ``src`` is a device view of the input (any row pitch);
-    ``out`` is filled by the server with a fresh w x h tensor."""
+    ``out`` is a w x h tensor the server fills (a view of its batch's output
+    allocation, made when first read)."""
     w: int
     h: int
     levels: int
@@ -49,11 +50,25 @@ class Request:
     inverse: bool = False
     src: Optional[torch.Tensor] = None
     arrival: float = 0.0
-    out: Optional[torch.Tensor] = None
     done: Optional[float] = None
     status: int = -1
     cost: int = 0
     tag: object = None
+    _slab: Optional[torch.Tensor] = field(default=None, repr=False)
+    _off: int = 0
+    _out: Optional[torch.Tensor] = field(default=None, repr=False)
+
+    @property
+    def out(self) -> Optional[torch.Tensor]:
+        if self._out is None and self._slab is not None:
+            n = self.w * self.h * ELEM[self.dtype]
+            self._out = self._slab[self._off:self._off + n].view(TDT[self.dtype]).view(self.h, self.w)
+        return self._out
+
+    @out.setter
+    def out(self, value: Optional[torch.Tensor]) -> None:
+        self._out = value
+        self._slab = None
 
     @property
     def latency(self) -> float:
@@ -167,11 +182,13 @@ class Server:
                 offs.append(total)
                 total += (r.w * r.h * ELEM[r.dtype] + 255) // 256 * 256
             slab = torch.empty(max(total, 256), dtype=torch.uint8, device=self.device)
+            base = slab.data_ptr()
             entries = []
             for r, off in zip(reqs, offs):
-                n = r.w * r.h * ELEM[r.dtype]
-                r.out = slab[off:off + n].view(TDT[r.dtype]).view(r.h, r.w)
-                entries.append(self._plan(r).request(r.src, r.out, r.inverse))
+                es = ELEM[r.dtype]
+                r._slab, r._off, r._out = slab, off, None
+                entries.append(dwt.DwtRequest(self._plan(r).handle, r.src.data_ptr(), r.src.stride(0) * es,
+                                              base + off, r.w * es, int(r.inverse)))
             dwt.submit(entries, status=status, stream=stream.cuda_stream)
             # read back on the batch's own stream: no synchronisation with
             # the other batches in flight
