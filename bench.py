@@ -84,6 +84,7 @@ SCHEME_SOURCE = {"rowcol": "k_rowcol.cu", "sweldens": "k_sweldens.cu", "iwahashi
                  "iwahashi*": "k_iwahashi_s.cu", "explosive": "k_explosive.cu", "explosive*": "k_explosive_s.cu",
                  "monolithic": "k_monolithic.cu", "monolithic*": "k_monolithic_s.cu",
                  "polyphase": "k_polyphase.cu", "polyphase*": "k_polyphase_s.cu", "convolution": "k_convolution.cu"}
+ALL_SCHEMES = list(SCHEME_SOURCE)
 
 
 def kernel_source_hash(scheme="monolithic*"):
