@@ -55,7 +55,7 @@ def parse():
     ap.add_argument("--levels", type=int, default=6)
     ap.add_argument("--wavelet", default="cdf97", choices=["cdf53", "cdf97"])
     ap.add_argument("--scheme", default="monolithic*")
-    ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--e2e-steps", type=int, default=100)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--mode", choices=["transform", "sweep", "batch", "serving"], default="transform")
     ap.add_argument("--sizes", default="1024,2048,4096,8192,16384", help="sweep: square sizes")
@@ -272,6 +272,41 @@ def time_calls(torch, fn, reps, flush=None, warm=2):
         e1.synchronize()
         ts.append(e0.elapsed_time(e1) * 1e3)  # us
     return statistics.median(ts)
+
+
+def host_link_gbs(torch, d, h_src, h_dst, streams, reps=5):
+    """Bandwidth of plain copies between pinned host memory and the device
+    (GB/s): host to device, device to host, and both directions at once on
+    two streams (GB/s each way)."""
+    nb = d.numel() * d.element_size()
+    d2 = torch.empty_like(d)
+    s0, s1 = streams
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            fn()
+        torch.cuda.synchronize()
+        return nb / ((time.perf_counter() - t0) / reps) / 1e9
+
+    def h2d():
+        with torch.cuda.stream(s0):
+            d2.copy_(h_src, non_blocking=True)
+
+    def d2h():
+        with torch.cuda.stream(s0):
+            h_dst.copy_(d, non_blocking=True)
+
+    def both():
+        h2d()
+        with torch.cuda.stream(s1):
+            h_dst.copy_(d, non_blocking=True)
+
+    out = {"h2d": timed(h2d), "d2h": timed(d2h), "h2d_and_d2h_concurrent": timed(both)}
+    del d2
+    return out
 
 
 def time_back_to_back(torch, fn, k, warm=2):
@@ -730,6 +765,13 @@ def main():
     e2e = {"value": whole_job_rate(2.0 * n * n * k2, world, ms2) / 1e9, "unit": UNIT,
            "h2d_bytes_per_step": 2 * n * n * 4, "d2h_bytes_per_step": 2 * n * n * 4,
            "pipelining": "two plans on two streams, steps alternating"}
+    # the host link bounds this number: plain copies of one image buffer
+    # (pinned host memory), each direction alone and both at once
+    link = host_link_gbs(torch, x, xh, chs[1], streams)
+    both = link["h2d_and_d2h_concurrent"]
+    e2e["host_link_gbs"] = link
+    e2e["link_bound_value"] = 2.0 * n * n / (2 * n * n * 4 / (both * 1e9)) / 1e9
+    e2e["frac_of_link_bound"] = e2e["value"] / e2e["link_bound_value"]
     plans[1].close()
 
     cpu = None
