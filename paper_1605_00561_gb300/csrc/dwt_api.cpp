@@ -314,6 +314,22 @@ int strip_height(int target, int ch, int ncs, int cap_warps, int halo, int chunk
   return best;
 }
 
+// Default strip height of a scheme.  Ten quadruple rows in general.  The
+// three-step schemes (Iwahashi, Explosive and their starred forms) with two
+// lifting pairs or degree-3 steps reach 8-10 quadruple rows vertically and
+// spend many instructions per row, so each strip's halo rows cost as much
+// as its own at that height; they take 32.  Monolithic, Monolithic* and
+// Polyphase* with DD 13/7 (a 6-row halo of merged degree-3 stencils) take
+// 24.  Measured on 8192^2 and 16384^2 at 10-32 rows.
+int default_strip_rows(int scheme, int wavelet) {
+  const bool three_step = scheme == DWT_IWAHASHI || scheme == DWT_IWAHASHI_S || scheme == DWT_EXPLOSIVE ||
+                          scheme == DWT_EXPLOSIVE_S;
+  if (three_step && wavelet != DWT_CDF53) return 32;
+  if (wavelet == DWT_DD137 && (scheme == DWT_MONOLITHIC || scheme == DWT_MONOLITHIC_S || scheme == DWT_POLYPHASE_S))
+    return 24;
+  return kDefaultStripRows;
+}
+
 // Chunk rows (quad rows per ring stage) of a kernel.
 int chunk_rows(const KernelInfo& ki) { return ki.load == SAMPLES ? ki.box_h / 2 : ki.box_h; }
 
@@ -366,7 +382,7 @@ struct dwt_plan_s {
   std::vector<ProfRec> pending;
   std::vector<cudaEvent_t> pool;
   int nstages = kDefaultStages;
-  int strip_rows = kDefaultStripRows;
+  int strip_rows = 0;  // 0: the default of the scheme a call runs (default_strip_rows)
   bool tile_set = false;  // the caller chose the tile: the autotuner's choice does not apply
   bool tuned = false;     // the autotuner cache was consulted
   std::mutex mu;
@@ -530,7 +546,8 @@ dwt_status level_geometry(const dwt_plan_s* p, const LaunchKey& key, LevelArgs& 
   // one strip per resident warp when the level is large enough: a single
   // wave, with strips as tall as that allows (less vertical halo)
   a.ncs = (a.cw + ki.uq - 1) / ki.uq;
-  a.T = strip_height(p->strip_rows, a.ch, a.ncs, cap, ki.up + ki.down, chunk_rows(ki));
+  const int target = p->strip_rows > 0 ? p->strip_rows : default_strip_rows(key.scheme, key.wavelet);
+  a.T = strip_height(target, a.ch, a.ncs, cap, ki.up + ki.down, chunk_rows(ki));
   a.nrs = (a.ch + a.T - 1) / a.T;
   // a level that does not fill the GPU once is latency-bound: a deeper
   // ring lets each (short) strip issue all its chunk loads at once, as long
@@ -975,7 +992,8 @@ dwt_status batch_submit(const dwt_request* reqs, int n, cudaStream_t s, int* d_s
       LevelArgs& a = b.a;
       level_dims(p, k, a);
       a.ncs = (a.cw + ki.uq - 1) / ki.uq;
-      a.T = strip_height(p->strip_rows, a.ch, a.ncs, cap, ki.up + ki.down, chunk_rows(ki));
+      a.T = strip_height(p->strip_rows > 0 ? p->strip_rows : kDefaultStripRows, a.ch, a.ncs, cap,
+                         ki.up + ki.down, chunk_rows(ki));
       a.nrs = (a.ch + a.T - 1) / a.T;
       a.nstages = nstages;
       b.cf = make_coefs(lifting_of(p->wavelet), p->norm, a.W, a.H, PASS_FUSED, inverse);
@@ -1341,7 +1359,7 @@ dwt_status dwt_plan_set_tile(dwt_plan p, int strip_rows, int stages) {
   if (!p || strip_rows < 0 || strip_rows > 1 << 20 || stages < 0 || stages > kMaxStages)
     return DWT_EINVAL;
   std::lock_guard<std::mutex> lk(p->mu);
-  p->strip_rows = strip_rows ? strip_rows : kDefaultStripRows;
+  p->strip_rows = strip_rows;
   p->nstages = stages ? stages : kDefaultStages;
   p->tile_set = strip_rows != 0 || stages != 0;
   return DWT_OK;
@@ -1350,8 +1368,8 @@ dwt_status dwt_plan_set_tile(dwt_plan p, int strip_rows, int stages) {
 dwt_status dwt_plan_get_tile(dwt_plan p, int* strip_rows, int* stages) {
   if (!p) return DWT_EINVAL;
   std::lock_guard<std::mutex> lk(p->mu);
-  apply_cache(p);
-  if (strip_rows) *strip_rows = p->strip_rows;
+  const int scheme = resolve_scheme(p);
+  if (strip_rows) *strip_rows = p->strip_rows > 0 ? p->strip_rows : default_strip_rows(scheme, p->wavelet);
   if (stages) *stages = p->nstages;
   return DWT_OK;
 }
@@ -1514,10 +1532,10 @@ dwt_status dwt_plan_autotune(dwt_plan p, dwt_stream stream) {
     *best = t;
     return true;
   };
-  // 1. the scheme, at the default tile
+  // 1. the scheme, each at its default tile
   Tuned best;
   float best_ms = 0.f;
-  p->strip_rows = kDefaultStripRows;
+  p->strip_rows = 0;
   p->nstages = kDefaultStages;
   for (int sc = DWT_ROWCOL; e == cudaSuccess && sc < NUM_SCHEMES; ++sc) {
     if (!scheme_supported(p->wavelet, p->dtype, sc)) continue;
@@ -1530,11 +1548,12 @@ dwt_status dwt_plan_autotune(dwt_plan p, dwt_stream stream) {
     }
   }
   // 2. the strip height of that scheme, then the ring depth
-  best.rows = kDefaultStripRows;
+  best.rows = best.scheme >= 0 ? default_strip_rows(best.scheme, p->wavelet) : kDefaultStripRows;
   best.stages = kDefaultStages;
   if (best.scheme >= 0) {
     p->scheme = best.scheme;
-    for (int rows : {6, 8, 12, 16, 24}) {
+    for (int rows : {6, 8, 10, 12, 16, 24, 32}) {
+      if (rows == best.rows) continue;
       p->strip_rows = rows;
       float t;
       if (time_it(&t) && t < best_ms) {

@@ -258,7 +258,7 @@ def test_autotune_scheme_and_tile_cached(dwt, tmp_path, monkeypatch):
     scheme = p.scheme
     rows, stages = dwt.dwt_plan_get_tile(p.handle)
     assert scheme in FLOAT_SCHEMES
-    assert rows in (6, 8, 10, 12, 16, 24) and 1 <= stages <= 4
+    assert rows in (6, 8, 10, 12, 16, 24, 32) and 1 <= stages <= 4
     # the tuned plan still computes the transform
     x = inputs.uniform_image(h, w, seed=77)
     ref = oracle.dwt2(x.astype(np.float64), oracle.CDF97, L)
@@ -276,6 +276,22 @@ def test_autotune_scheme_and_tile_cached(dwt, tmp_path, monkeypatch):
     assert dwt.dwt_plan_get_tile(r.handle) == (8, 3)
     for plan in (p, q, r):
         plan.close()
+
+
+def test_default_strip_rows_follow_the_scheme(dwt, tmp_path, monkeypatch):
+    """Without a tile from the caller or the autotuner, each scheme takes its
+    own default strip height; dwt_plan_set_tile(0, 0) returns to it."""
+    monkeypatch.setenv("DWT_AUTOTUNE_CACHE", str(tmp_path / "empty.txt"))
+    cases = [("monolithic*", "cdf97", 10), ("sweldens", "dd137", 10), ("iwahashi", "cdf53", 10),
+             ("iwahashi*", "cdf97", 32), ("explosive", "dd137", 32), ("monolithic*", "dd137", 24)]
+    for scheme, wavelet, rows in cases:
+        p = dwt.Plan(512, 384, wavelet, 2, "f32", scheme=scheme)
+        assert dwt.dwt_plan_get_tile(p.handle) == (rows, 2), (scheme, wavelet)
+        dwt.dwt_plan_set_tile(p.handle, 6, 3)
+        assert dwt.dwt_plan_get_tile(p.handle) == (6, 3)
+        dwt.dwt_plan_set_tile(p.handle, 0, 0)
+        assert dwt.dwt_plan_get_tile(p.handle) == (rows, 2)
+        p.close()
 
 
 def test_plan_calls_replay_from_a_cuda_graph(dwt):
