@@ -505,6 +505,31 @@ def run_batch(a):
     ok_status = int(status.abs().sum()) == 0
     exact = all(torch.equal(x, y) for x, y in zip(imgs[len(imgs) // 2:], back[len(back) // 2:]))
 
+    # the same batch with every row padded to a 128-byte pitch (the layout
+    # cudaMallocPitch gives): every plane is then 16-byte aligned and TMA
+    # loads all of it; with tightly packed rows of odd widths the kernels
+    # fall back to box copies for those planes
+    def pitched(t):
+        hh, ww = t.shape
+        es = t.element_size()
+        buf = torch.empty((hh, (ww * es + 127) // 128 * 128 // es), dtype=t.dtype, device=t.device)
+        view = buf[:, :ww]
+        view.copy_(t)
+        return view
+
+    imgs_p = [pitched(x) for x in imgs]
+    coefs_p = [pitched(c) for c in coefs]
+    back_p = [pitched(y) for y in back]
+    fwd_p = [p.request(x, c) for p, x, c in zip(plans, imgs_p, coefs_p)]
+    inv_p = [p.request(c, y, True) for p, c, y in zip(plans, coefs_p, back_p)]
+    t_fwd_p = time_back_to_back(torch, lambda: dwt.submit(fwd_p, status=status), a.steps, warm=a.warmup)
+    t_inv_p = time_back_to_back(torch, lambda: dwt.submit(inv_p, status=status), a.steps, warm=a.warmup)
+    torch.cuda.synchronize()
+    ok_status = ok_status and int(status.abs().sum()) == 0
+    exact_p = all(torch.equal(x, y) for x, y in zip(imgs_p[len(imgs) // 2:], back_p[len(back) // 2:]))
+    same_p = all(torch.equal(c, cp) for c, cp in zip(coefs, coefs_p))
+    del imgs_p, coefs_p, back_p, fwd_p, inv_p
+
     # one launch per image (a batch of one each), and per-level launches per
     # image through each plan (its own scheme, default tile)
     singles = [[r] for r in fwd]
@@ -543,6 +568,10 @@ def run_batch(a):
         "one_launch_per_image_us": t_single, "per_level_launches_us": t_plans,
         "speedup_vs_one_launch_per_image": t_single / t_fwd, "speedup_vs_per_level": t_plans / t_fwd,
         "autotuned_tile": {"class_area_cuts": cuts, "strip_rows": choice, "stages": stages, "log": tune_log},
+        "pitched_128b_rows": {"batch_fwd_us": t_fwd_p, "batch_inv_us": t_inv_p,
+                              "batch_fwd_gpx_s": pixels / t_fwd_p / 1e3, "batch_inv_gpx_s": pixels / t_inv_p / 1e3,
+                              "batch_fwd_hbm_frac": ab / (t_fwd_p * 1e-6) / 1e9 / peak,
+                              "int_round_trip_exact": exact_p, "coefficients_equal_packed": same_p},
         "status_ok": ok_status, "int_round_trip_exact": exact,
         "f16s_97_fwd_us": t_f16, "f16s_97_gpx_s": f16_px / t_f16 / 1e3,
         "f16s_97_max_abs_err_vs_fp64": max(errs), "f32_97_max_abs_err_vs_fp64": max(errs32),
