@@ -66,7 +66,8 @@ __device__ __noinline__ bool go(const BatchLevel& L, int cs, int rs, bool new_le
     // the maps were uploaded by a copy, and an earlier batch may have left
     // another map at the same address in the tensor-map cache
     constexpr int nmaps = C::LOAD == SAMPLES ? 1 : 4;
-    for (int i = 0; i < nmaps; ++i) ptx::fence_tensormap_acquire(&L.maps.m[i]);
+    for (int i = 0; i < nmaps; ++i)
+      if ((L.a.src_tma >> i) & 1) ptx::fence_tensormap_acquire(&L.maps.m[i]);
   }
   return run_strip<C>(L.a, L.maps, L.cf, kNoTaps, cs, rs, ring, kStageStride, bars, ctr);
 }

@@ -287,6 +287,25 @@ bool encode_2d(CUtensorMap* m, int dtype, const void* base, int w, int h, size_t
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// Tensor maps of a level's source planes.  Returns the planes whose map is
+// valid (bit p for plane p): the kernels load those by TMA and copy the
+// others (a plane whose base or row pitch is not 16-byte aligned, as the HL
+// and HH bands at column ceil(w/2) of most odd-width coefficient planes).
+int encode_level_maps(TmaMaps* maps, int dtype, const LevelArgs& a, const KernelInfo& ki, size_t es) {
+  std::memset(maps, 0, sizeof *maps);
+  if (a.W < 2 || a.H < 2) return 0;
+  if (ki.load == SAMPLES)
+    return encode_2d(&maps->m[0], dtype, a.src[0], a.W, a.H, (size_t)a.src_pitch[0] * es, ki.box_w, ki.box_h)
+               ? 1
+               : 0;
+  const int pw[4] = {a.cw, a.fw, a.cw, a.fw}, ph[4] = {a.ch, a.ch, a.fh, a.fh};
+  int mask = 0;
+  for (int i = 0; i < 4; ++i)
+    if (encode_2d(&maps->m[i], dtype, a.src[i], pw[i], ph[i], (size_t)a.src_pitch[i] * es, ki.box_w, ki.box_h))
+      mask |= 1 << i;
+  return mask;
+}
+
 size_t elem_size(int dtype) { return dtype == F16S ? 2 : 4; }
 
 // Quad rows per strip.  Strips of about ten rows keep several waves of
@@ -569,22 +588,7 @@ dwt_status launch(dwt_plan_s* p, const LaunchKey& key, LevelArgs& a, const Coefs
   a.status = p->d_status;
 
   TmaMaps maps;
-  std::memset(&maps, 0, sizeof maps);
-  a.src_tma = 0;
-  if (a.W >= 2 && a.H >= 2) {
-    const size_t es = p->es;
-    if (ki.load == SAMPLES) {
-      a.src_tma = encode_2d(&maps.m[0], p->dtype, a.src[0], a.W, a.H, (size_t)a.src_pitch[0] * es,
-                            ki.box_w, ki.box_h);
-    } else {
-      const int pw[4] = {a.cw, a.fw, a.cw, a.fw}, ph[4] = {a.ch, a.ch, a.fh, a.fh};
-      bool ok = true;
-      for (int i = 0; i < 4 && ok; ++i)
-        ok = encode_2d(&maps.m[i], p->dtype, a.src[i], pw[i], ph[i], (size_t)a.src_pitch[i] * es,
-                       ki.box_w, ki.box_h);
-      a.src_tma = ok;
-    }
-  }
+  a.src_tma = encode_level_maps(&maps, p->dtype, a, ki, p->es);
 
   ProfRec rec{-1, nullptr, nullptr, 0.0};
   if (p->profiling) {
@@ -1132,21 +1136,7 @@ dwt_status batch_submit(const dwt_request* reqs, int n, cudaStream_t s, int* d_s
                                 reqs[i].out_pitch, ll.data(), ll_pitch[i].data());
     fused_io(io, inverse, a);
     a.status = status + i;
-    a.src_tma = 0;
-    const KernelInfo& ki = kinfo[b.kind];
-    if (a.W >= 2 && a.H >= 2) {
-      if (ki.load == SAMPLES) {
-        a.src_tma = encode_2d(&b.maps.m[0], p->dtype, a.src[0], a.W, a.H, (size_t)a.src_pitch[0] * p->es,
-                              ki.box_w, ki.box_h);
-      } else {
-        const int pw[4] = {a.cw, a.fw, a.cw, a.fw}, ph[4] = {a.ch, a.ch, a.fh, a.fh};
-        bool ok = true;
-        for (int j = 0; j < 4 && ok; ++j)
-          ok = encode_2d(&b.maps.m[j], p->dtype, a.src[j], pw[j], ph[j], (size_t)a.src_pitch[j] * p->es,
-                         ki.box_w, ki.box_h);
-        a.src_tma = ok;
-      }
-    }
+    a.src_tma = encode_level_maps(&b.maps, p->dtype, a, kinfo[b.kind], p->es);
   }
   unsigned char* h = static_cast<unsigned char*>(st.host);
   std::memcpy(h, levels.data(), sizeof(BatchLevel) * nl);
@@ -1273,11 +1263,7 @@ dwt_status forward_on_scratch(int w, int h, int wavelet, int levels, int dtype, 
     a.nstages = (long long)a.ncs * a.nrs < cap ? kMaxStages : kDefaultStages;
     a.status = d_status;
     TmaMaps maps;
-    std::memset(&maps, 0, sizeof maps);
-    a.src_tma = 0;
-    if (a.W >= 2 && a.H >= 2)
-      a.src_tma = encode_2d(&maps.m[0], dtype, a.src[0], a.W, a.H, (size_t)a.src_pitch[0] * es,
-                            ki.box_w, ki.box_h);
+    a.src_tma = encode_level_maps(&maps, dtype, a, ki, es);
     const LaunchCall call{&a, &maps, &cf, &ct, s};
     const cudaError_t e = call_kernel(key, kDefaultStages, call);
     if (e != cudaSuccess) return from_cuda(e);

@@ -78,7 +78,7 @@ struct LevelArgs {
   long long src_pitch[4];
   void* dst[4];
   long long dst_pitch[4];
-  int src_tma;   // 1: tensor maps are valid for every source plane
+  int src_tma;   // bit p: the tensor map of source plane p is valid (TMA loads it)
   int* status;   // device error word (bit 0: a bounded wait ran out)
 };
 

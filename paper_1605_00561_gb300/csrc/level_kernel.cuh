@@ -239,13 +239,6 @@ struct Strip {
       return ok;
     }
   }
-  __device__ __forceinline__ bool chunk_by_tma(int c) const {
-    if (!a.src_tma || a.W < 2 || a.H < 2) return false;
-    const int y0 = yfirst + c * C::CH;
-    const bool rows = C::LOAD == SAMPLES ? (2 * y0 >= 0 && 2 * y0 + C::ROWS <= a.H)
-                                         : (y0 >= 0 && y0 + C::CH <= a.fh);
-    return rows && cols_by_tma();
-  }
   // ---- fills ---------------------------------------------------------------
   // The box a TMA load would bring, copied by the lanes with cp.async: for
   // chunks the TMA engine cannot take (rows to mirror at the top or bottom,
@@ -367,16 +360,40 @@ struct Strip {
       ptx::mbar_arrive(bar);
     } else {
       // four subband planes; the lane covers quads mfirst + QL*lane + (0..QL-1)
-      if (box && a.src_tma && y0 >= 0 && y0 + C::CH <= a.fh) {
+      const int tma = a.src_tma & 15;
+      if (box && tma && y0 >= 0 && y0 + C::CH <= a.fh) {
+        const int x0 = align_down(mfirst, C::A);
+        if (tma == 15) {
+          if (lane == 0) {
+            ptx::fence_proxy_async_smem();
+            ptx::mbar_arrive_expect_tx(bar, 4 * C::BOX_BYTES);
+#pragma unroll
+            for (int p = 0; p < 4; ++p) ptx::tma_load_2d(plane(s, p), &maps.m[p], x0, y0, bar);
+          } else {
+            ptx::mbar_arrive(bar);
+          }
+          return;
+        }
+        // planes with a tensor map by TMA, the others (a base or pitch that
+        // is not 16-byte aligned) by box copies; the rows lie inside every
+        // plane.  The barrier completes when the TMA bytes have landed and
+        // every lane's copies are done (one arrival per lane).
         if (lane == 0) {
           ptx::fence_proxy_async_smem();
-          ptx::mbar_arrive_expect_tx(bar, 4 * C::BOX_BYTES);
+          ptx::mbar_expect_tx(bar, (uint32_t)__popc(tma) * C::BOX_BYTES);
 #pragma unroll
           for (int p = 0; p < 4; ++p)
-            ptx::tma_load_2d(plane(s, p), &maps.m[p], align_down(mfirst, C::A), y0, bar);
-        } else {
-          ptx::mbar_arrive(bar);
+            if ((tma >> p) & 1) ptx::tma_load_2d(plane(s, p), &maps.m[p], x0, y0, bar);
         }
+#pragma unroll 1
+        for (int p = 0; p < 4; ++p) {
+          if ((tma >> p) & 1) continue;
+          const int pw = (p & 1) ? a.fw : a.cw;
+#pragma unroll 1
+          for (int r = 0; r < C::CH; ++r)
+            copy_box_row(plane(s, p) + r * C::ROWE, src_plane(p) + (long long)(y0 + r) * a.src_pitch[p], x0, pw);
+        }
+        ptx::cp_async_arrive(bar);
         return;
       }
       if (box) {
@@ -781,14 +798,10 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, C::MIN_WARPS / kWarpsPerCta
   if (lane == 0) {
     for (int s = 0; s < NS; ++s) ptx::mbar_init(&bars[s], 32);
     ptx::fence_barrier_init();
-    if (a.src_tma) {
-      ptx::prefetch_tensormap(&maps.m[0]);
-      if constexpr (C::LOAD == SUBBANDS) {
-        ptx::prefetch_tensormap(&maps.m[1]);
-        ptx::prefetch_tensormap(&maps.m[2]);
-        ptx::prefetch_tensormap(&maps.m[3]);
-      }
-    }
+    constexpr int nmaps = C::LOAD == SUBBANDS ? 4 : 1;
+#pragma unroll
+    for (int p = 0; p < nmaps; ++p)
+      if ((a.src_tma >> p) & 1) ptx::prefetch_tensormap(&maps.m[p]);
   }
   __syncwarp();
   int cs, rs;
