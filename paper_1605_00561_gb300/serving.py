@@ -37,6 +37,13 @@ ELEM = {"f32": 4, "f16s": 2, "i32": 4}
 TDT = {"f32": torch.float32, "f16s": torch.float16, "i32": torch.int32}
 
 
+def out_pitch(w: int, dtype: str) -> int:
+    """Row pitch (bytes) of a served output: rows padded to 128 bytes, so
+    that the kernels store whole aligned vectors and an inverse of the
+    output can load its planes by TMA."""
+    return (w * ELEM[dtype] + 127) // 128 * 128
+
+
 @dataclass
 class Request:
     """One transform.  ``src`` is a device view of the input (any row pitch);
@@ -61,8 +68,9 @@ class Request:
     @property
     def out(self) -> Optional[torch.Tensor]:
         if self._out is None and self._slab is not None:
-            n = self.w * self.h * ELEM[self.dtype]
-            self._out = self._slab[self._off:self._off + n].view(TDT[self.dtype]).view(self.h, self.w)
+            pitch = out_pitch(self.w, self.dtype)
+            rows = self._slab[self._off:self._off + pitch * self.h].view(TDT[self.dtype])
+            self._out = rows.view(self.h, pitch // ELEM[self.dtype])[:, :self.w]
         return self._out
 
     @out.setter
@@ -76,11 +84,12 @@ class Request:
 
 
 def request_bytes(r: Request) -> int:
-    """Device bytes a request holds while in flight: its output plane and
-    the LL ping-pong scratch of its batch work area (rows of ceil(w/2)
-    elements at a 128-byte pitch, ceil(h/2) + ceil(h/4) of them)."""
+    """Device bytes a request holds while in flight: its output plane (rows
+    at a 128-byte pitch) and the LL ping-pong scratch of its batch work area
+    (rows of ceil(w/2) elements at a 128-byte pitch, ceil(h/2) + ceil(h/4)
+    of them)."""
     es = ELEM[r.dtype]
-    out = r.w * r.h * es
+    out = out_pitch(r.w, r.dtype) * r.h
     if r.levels < 2:
         return out
     w1, h1 = (r.w + 1) // 2, (r.h + 1) // 2
@@ -180,7 +189,7 @@ class Server:
             offs, total = [], 0
             for r in reqs:
                 offs.append(total)
-                total += (r.w * r.h * ELEM[r.dtype] + 255) // 256 * 256
+                total += (out_pitch(r.w, r.dtype) * r.h + 255) // 256 * 256
             slab = torch.empty(max(total, 256), dtype=torch.uint8, device=self.device)
             base = slab.data_ptr()
             entries = []
@@ -188,7 +197,7 @@ class Server:
                 es = ELEM[r.dtype]
                 r._slab, r._off, r._out = slab, off, None
                 entries.append(dwt.DwtRequest(self._plan(r).handle, r.src.data_ptr(), r.src.stride(0) * es,
-                                              base + off, r.w * es, int(r.inverse)))
+                                              base + off, out_pitch(r.w, r.dtype), int(r.inverse)))
             dwt.submit(entries, status=status, stream=stream.cuda_stream)
             # read back on the batch's own stream: no synchronisation with
             # the other batches in flight
