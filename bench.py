@@ -61,6 +61,10 @@ def parse():
     ap.add_argument("--sizes", default="1024,2048,4096,8192,16384", help="sweep: square sizes")
     ap.add_argument("--schemes", default="all", help="sweep: comma-separated scheme names")
     ap.add_argument("--reps", type=int, default=10, help="sweep: timed repetitions per config")
+    ap.add_argument("--wavelets", default="cdf53,cdf97,dd137", help="sweep: comma-separated float wavelets")
+    ap.add_argument("--sweep-levels", default="1,6", help="sweep: comma-separated level counts")
+    ap.add_argument("--no-autotune", action="store_true", help="sweep: skip the autotuner column")
+    ap.add_argument("--no-int", action="store_true", help="sweep: skip the reversible 5/3 rows")
     ap.add_argument("--out", default=None, help="sweep/batch/serving: also write a markdown table here")
     ap.add_argument("--batch-n", type=int, default=256)
     ap.add_argument("--batch-lo", type=int, default=256)
@@ -343,8 +347,8 @@ def run_sweep(a):
         c = torch.empty_like(x)
         y = torch.empty_like(x)
         resident = 2 * n * n * 4 <= l2
-        for wl in ("cdf53", "cdf97", "dd137"):
-            for L in (1, 6):
+        for wl in a.wavelets.split(","):
+            for L in [int(v) for v in a.sweep_levels.split(",")]:
                 for sc in schemes:
                     if wl == "dd137" and sc in DD_UNSUPPORTED:
                         continue
@@ -361,6 +365,9 @@ def run_sweep(a):
                                      "gpx_s": n * n / t / 1e3, "hbm_frac": ab / (t * 1e-6) / 1e9 / peak,
                                      "l2": "flushed" if resident else "larger than L2"})
                 # the autotuner's choice for this configuration
+                if a.no_autotune:
+                    tuned[(n, wl, L)] = ("-", (0, 0))
+                    continue
                 plan = dwt.Plan(n, n, wl, L, "f32")
                 dwt.dwt_plan_autotune(plan.handle)
                 tuned[(n, wl, L)] = (plan.scheme, dwt.dwt_plan_get_tile(plan.handle))
@@ -373,6 +380,8 @@ def run_sweep(a):
     gi = torch.Generator(device="cuda")
     gi.manual_seed(7)
     int_shapes = [(n, n) for n in sizes if n >= 4096] + ([(5001, 3333)] if max(sizes) >= 4096 else [])
+    if a.no_int:
+        int_shapes = []
     for (w, h) in int_shapes:
         x = torch.randint(0, 4096, (h, w), generator=gi, device="cuda", dtype=torch.int32)
         c = torch.empty_like(x)
