@@ -349,6 +349,19 @@ int default_strip_rows(int scheme, int wavelet) {
   return kDefaultStripRows;
 }
 
+// Rows of strips one resident wave holds, for the kernels' dealt strip-row
+// order (strip_coords): vertically adjacent strips then run in consecutive
+// waves and the rows they share come from L2.  Only tall strips (24 rows or
+// more) use it: their neighbours, run in the same wave, read the shared
+// rows a long strip apart and miss L2 (8192^2 Iwahashi 9/7 at 32 rows: 358
+// MB of DRAM reads against 312 MB dealt, and 3-7 % faster at 16384^2).
+// Short strips share rows a few row steps apart in the same wave, which
+// already hits L2; dealt, they read 2 % more from DRAM.  0: row by row.
+int wave_rows(const LevelArgs& a, int cap) {
+  if (a.T < 24) return 0;
+  return std::max(1, cap / std::max(1, a.ncs > 2 ? a.ncs - 2 : a.ncs));
+}
+
 // Chunk rows (quad rows per ring stage) of a kernel.
 int chunk_rows(const KernelInfo& ki) { return ki.load == SAMPLES ? ki.box_h / 2 : ki.box_h; }
 
@@ -568,6 +581,7 @@ dwt_status level_geometry(const dwt_plan_s* p, const LaunchKey& key, LevelArgs& 
   const int target = p->strip_rows > 0 ? p->strip_rows : default_strip_rows(key.scheme, key.wavelet);
   a.T = strip_height(target, a.ch, a.ncs, cap, ki.up + ki.down, chunk_rows(ki));
   a.nrs = (a.ch + a.T - 1) / a.T;
+  a.wave_rows = wave_rows(a, cap);
   // a level that does not fill the GPU once is latency-bound: a deeper
   // ring lets each (short) strip issue all its chunk loads at once, as long
   // as the level still fits one wave with the larger shared-memory ring
@@ -1260,6 +1274,7 @@ dwt_status forward_on_scratch(int w, int h, int wavelet, int levels, int dtype, 
     a.ncs = (a.cw + ki.uq - 1) / ki.uq;
     a.T = strip_height(kDefaultStripRows, a.ch, a.ncs, cap, ki.up + ki.down, chunk_rows(ki));
     a.nrs = (a.ch + a.T - 1) / a.T;
+    a.wave_rows = wave_rows(a, cap);
     a.nstages = (long long)a.ncs * a.nrs < cap ? kMaxStages : kDefaultStages;
     a.status = d_status;
     TmaMaps maps;

@@ -72,7 +72,8 @@ struct LevelArgs {
   // Strips: column strip cs covers useful quads [cs*UQ, cs*UQ+UQ); row
   // strip rs covers quad rows [rs*T, rs*T+T); strip index rs*ncs + cs.
   int ncs, nrs, T;
-  int nstages;  // ring depth used (<= kMaxStages)
+  int wave_rows;  // strip rows of one resident wave (dispatch order, see strip_coords); 0: row by row
+  int nstages;    // ring depth used (<= kMaxStages)
   // Sources and destinations (element pitches).
   const void* src[4];
   long long src_pitch[4];

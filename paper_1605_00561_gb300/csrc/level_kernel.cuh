@@ -651,20 +651,45 @@ struct Strip {
   }
 };
 
+// Strip row of the j-th row of strips in dispatch order, when one resident
+// wave holds P rows of strips.  The rows are dealt to the W = ceil(nrs / P)
+// waves round-robin (wave w takes rows w, w + W, w + 2W, ...), so that
+// vertically adjacent strips run in consecutive waves: the halo rows a strip
+// reads first are the rows its upper neighbour read last, just before, and
+// they come from L2.  (Run in the same wave, the two strips read them a
+// strip's duration apart, with a wave's worth of traffic in between.)  A
+// bijection on [0, nrs): wave w holds ceil((nrs - w) / W) rows.
+__device__ __forceinline__ int dealt_row(int j, int nrs, int P) {
+  if (P <= 0 || P >= nrs) return j;
+  const int W = (nrs + P - 1) / P;
+  const int q = nrs / W, r = nrs % W;
+  int w, k;
+  if (j < r * (q + 1)) {
+    w = j / (q + 1);
+    k = j - w * (q + 1);
+  } else {
+    const int jj = j - r * (q + 1);
+    w = r + jj / q;
+    k = jj - (w - r) * q;
+  }
+  return k * W + w;
+}
+
 // Strip order: the two border columns first (their halo handling makes
-// them the longest), then the interior row by row.  Blocks are dispatched
-// in this order, so the long strips start in the first wave.
-__device__ __forceinline__ void strip_coords(int s, int ncs, int nrs, int& cs, int& rs) {
+// them the longest), then the interior, one row of strips after another in
+// the dealt row order.  Blocks are dispatched in this order, so the long
+// strips start in the first wave.
+__device__ __forceinline__ void strip_coords(int s, int ncs, int nrs, int wave_rows, int& cs, int& rs) {
   if (ncs <= 2) {
     cs = s % ncs;
-    rs = s / ncs;
+    rs = dealt_row(s / ncs, nrs, wave_rows);
   } else if (s < 2 * nrs) {
     cs = (s & 1) ? ncs - 1 : 0;
     rs = s >> 1;
   } else {
     const int i = s - 2 * nrs;
     cs = 1 + i % (ncs - 2);
-    rs = i / (ncs - 2);
+    rs = dealt_row(i / (ncs - 2), nrs, wave_rows);
   }
 }
 
@@ -805,7 +830,7 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, C::MIN_WARPS / kWarpsPerCta
   }
   __syncwarp();
   int cs, rs;
-  strip_coords(strip, a.ncs, a.nrs, cs, rs);
+  strip_coords(strip, a.ncs, a.nrs, a.wave_rows, cs, rs);
   // the previous level's kernel may still be running: every read and write
   // of level data comes after this point
   ptx::wait_prerequisites();
