@@ -5,7 +5,7 @@
 namespace dwt {
 
 bool group_polyphase(const LaunchKey& k, int ns, KernelInfo* info, const LaunchCall* call, cudaError_t* err) {
-  return dev::fused_float<POLYPHASE>(k, ns, info, call, err);
+  return dev::fused_float<POLYPHASE, true>(k, ns, info, call, err);
 }
 
 }  // namespace dwt
