@@ -20,21 +20,23 @@ inline bool run(int nstages, KernelInfo* info, const LaunchCall* call, cudaError
 }
 
 // Quadruples per lane: four (128-bit vectors, fewer instructions and
-// shuffles per sample) except for Convolution and the unstarred Polyphase,
-// whose windows and stencils at four exceed the register file (and, for
-// Polyphase with two pairs, what the compiler handles).  A ring stage holds
-// the same bytes either way.
+// shuffles per sample) except for Convolution, whose windows at four exceed
+// the register file, and the unstarred Polyphase with CDF 5/3, which the
+// compiler does not build at four (it fails within 128 registers).  A ring
+// stage holds the same bytes either way.
 template <int SCHEME, int WL>
-constexpr int kQuadsPerLane = (SCHEME == POLYPHASE || SCHEME == CONVOLUTION) ? 2 : 4;
+constexpr int kQuadsPerLane = (SCHEME == CONVOLUTION || (SCHEME == POLYPHASE && WL == W53)) ? 2 : 4;
 
 // Resident warps per SM the register budget is cut for: 16 (128 registers)
 // in general; 12 (168 registers) for the three-step schemes with two pairs
-// or degree-3 steps, which need them at four quadruples per lane (DD 13/7
-// runs 1.3-2.2x faster at 12 than squeezed into 128 registers); 8 for
-// Convolution.
+// or degree-3 steps and for the unstarred Polyphase with two pairs, which
+// need them at four quadruples per lane (DD 13/7 runs 1.3-2.2x faster at 12
+// than squeezed into 128 registers; Polyphase 9/7 at four quadruples and 12
+// warps is 8-16 % faster at 8192^2 than at two and 16); 8 for Convolution.
 template <int SCHEME, int WL>
 constexpr int kMinWarps =
     SCHEME == CONVOLUTION ? 8
+    : (SCHEME == POLYPHASE && WL == W97) ? 12
     : ((WL == W97 || WL == WDD) &&
        (SCHEME == IWAHASHI || SCHEME == IWAHASHI_S || SCHEME == EXPLOSIVE || SCHEME == EXPLOSIVE_S))
         ? 12
