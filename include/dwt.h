@@ -113,9 +113,10 @@ dwt_status dwt_plan_set_scheme(dwt_plan plan, dwt_scheme scheme);
 /* Tile shape of the kernels (autotuner knobs).  strip_rows: target number
  * of quadruple rows a warp streams (0 = the default of the scheme a call
  * runs: 10; 32 for Iwahashi, Iwahashi*, Explosive and Explosive* with CDF
- * 9/7 or DD 13/7; 24 for Monolithic, Monolithic* and Polyphase* with DD
- * 13/7); a level too small to fill the GPU once with such strips uses
- * shorter ones, down to 2 rows.
+ * 9/7 or DD 13/7 and for Polyphase; 32 (5/3) or 48 (9/7) for Convolution;
+ * 24 for Monolithic, Monolithic* and Polyphase* with DD 13/7); a level too
+ * small to fill the GPU once with such strips uses shorter ones, down to 2
+ * rows.
  * stages: depth of each warp's shared-memory ring of row chunks, 1..4
  * (0 = default 2); deeper rings keep more loads in flight per warp,
  * shallower ones let more warps reside.  Errors: DWT_EINVAL for values out

@@ -333,17 +333,22 @@ int strip_height(int target, int ch, int ncs, int cap_warps, int halo, int chunk
   return best;
 }
 
-// Default strip height of a scheme.  Ten quadruple rows in general.  The
-// three-step schemes (Iwahashi, Explosive and their starred forms) with two
-// lifting pairs or degree-3 steps reach 8-10 quadruple rows vertically and
-// spend many instructions per row, so each strip's halo rows cost as much
-// as its own at that height; they take 32.  Monolithic, Monolithic* and
-// Polyphase* with DD 13/7 (a 6-row halo of merged degree-3 stencils) take
-// 24.  Measured on 8192^2 and 16384^2 at 10-32 rows.
+// Default strip height of a scheme.  Ten quadruple rows in general.  Every
+// strip also recomputes the rows of its vertical halo, so schemes that
+// spend many instructions per row take taller strips: the three-step
+// schemes (Iwahashi, Explosive and their starred forms) with two lifting
+// pairs or degree-3 steps (8-10 halo rows) and the unstarred Polyphase take
+// 32, Convolution 32 (5/3) or 48 (9/7), and Monolithic, Monolithic* and
+// Polyphase* with DD 13/7 (a 6-row halo of merged degree-3 stencils) 24.
+// Measured on 8192^2 and 16384^2 at 10-48 rows: Polyphase 9/7 at 8192^2
+// one level takes 164 us at 10 rows and 144 us at 32, Convolution 9/7 492
+// us at 10 and 356 us at 48; the schemes left at 10 are fastest there.
 int default_strip_rows(int scheme, int wavelet) {
   const bool three_step = scheme == DWT_IWAHASHI || scheme == DWT_IWAHASHI_S || scheme == DWT_EXPLOSIVE ||
                           scheme == DWT_EXPLOSIVE_S;
   if (three_step && wavelet != DWT_CDF53) return 32;
+  if (scheme == DWT_POLYPHASE) return 32;
+  if (scheme == DWT_CONVOLUTION) return wavelet == DWT_CDF53 ? 32 : 48;
   if (wavelet == DWT_DD137 && (scheme == DWT_MONOLITHIC || scheme == DWT_MONOLITHIC_S || scheme == DWT_POLYPHASE_S))
     return 24;
   return kDefaultStripRows;
@@ -1553,7 +1558,7 @@ dwt_status dwt_plan_autotune(dwt_plan p, dwt_stream stream) {
   best.stages = kDefaultStages;
   if (best.scheme >= 0) {
     p->scheme = best.scheme;
-    for (int rows : {6, 8, 10, 12, 16, 24, 32}) {
+    for (int rows : {6, 8, 10, 12, 16, 24, 32, 48}) {
       if (rows == best.rows) continue;
       p->strip_rows = rows;
       float t;

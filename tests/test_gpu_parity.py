@@ -258,7 +258,7 @@ def test_autotune_scheme_and_tile_cached(dwt, tmp_path, monkeypatch):
     scheme = p.scheme
     rows, stages = dwt.dwt_plan_get_tile(p.handle)
     assert scheme in FLOAT_SCHEMES
-    assert rows in (6, 8, 10, 12, 16, 24, 32) and 1 <= stages <= 4
+    assert rows in (6, 8, 10, 12, 16, 24, 32, 48) and 1 <= stages <= 4
     # the tuned plan still computes the transform
     x = inputs.uniform_image(h, w, seed=77)
     ref = oracle.dwt2(x.astype(np.float64), oracle.CDF97, L)
@@ -283,7 +283,8 @@ def test_default_strip_rows_follow_the_scheme(dwt, tmp_path, monkeypatch):
     own default strip height; dwt_plan_set_tile(0, 0) returns to it."""
     monkeypatch.setenv("DWT_AUTOTUNE_CACHE", str(tmp_path / "empty.txt"))
     cases = [("monolithic*", "cdf97", 10), ("sweldens", "dd137", 10), ("iwahashi", "cdf53", 10),
-             ("iwahashi*", "cdf97", 32), ("explosive", "dd137", 32), ("monolithic*", "dd137", 24)]
+             ("iwahashi*", "cdf97", 32), ("explosive", "dd137", 32), ("monolithic*", "dd137", 24),
+             ("polyphase", "cdf53", 32), ("convolution", "cdf97", 48), ("convolution", "cdf53", 32)]
     for scheme, wavelet, rows in cases:
         p = dwt.Plan(512, 384, wavelet, 2, "f32", scheme=scheme)
         assert dwt.dwt_plan_get_tile(p.handle) == (rows, 2), (scheme, wavelet)
