@@ -133,6 +133,22 @@ def test_textured_8192_cdf97_six_levels_full_compare(dwt):
     assert np.abs(y - x).max() <= TOL_ROUND_TRIP
 
 
+@pytest.mark.parametrize("scheme,wavelet", [("iwahashi*", "cdf97"), ("explosive", "cdf97"),
+                                            ("polyphase", "cdf97"), ("convolution", "cdf97"),
+                                            ("monolithic*", "dd137")])
+def test_tall_strip_schemes_8192_full_compare(dwt, scheme, wavelet):
+    """Schemes whose default strips are 24-48 rows tall: at 8192^2 their
+    strip rows are dealt over several resident waves (the dispatch order of
+    tall strips), which small images never reach.  Every coefficient and
+    every reconstructed sample is compared."""
+    n, L = 8192, 1
+    x = inputs.textured_image(n, n, seed=3)
+    ref = oracle.dwt2(x.astype(np.float64), {"cdf97": oracle.CDF97, "dd137": oracle.DD137}[wavelet], L)
+    c, y, _ = run_fwd_inv(dwt, x, wavelet, L, "f32", scheme)
+    assert np.abs(c - ref).max() <= TOL_F32
+    assert np.abs(y - x).max() <= TOL_ROUND_TRIP
+
+
 @pytest.mark.parametrize("h,w", [(4096, 4096), (3333, 5001)])
 def test_int53_config_sizes_bit_exact(dwt, h, w):
     x = inputs.int12_image(h, w, seed=7)
