@@ -84,6 +84,57 @@ def test_dd137_forward_inverse_vs_oracle(dwt, scheme, h, w, L):
     assert np.abs(y - x).max() <= TOL_ROUND_TRIP, "round trip"
 
 
+def zeta_tol(ref):
+    # the paper's scaling grows LL by 2 per level (zeta^2 = 2): FP32 error
+    # scales with the magnitudes, so the bar is relative to the largest
+    return TOL_F32 + 2e-5 * float(np.abs(ref).max())
+
+
+@pytest.mark.parametrize("scheme", FLOAT_SCHEMES)
+@pytest.mark.parametrize("wavelet", ["cdf53", "cdf97"])
+@pytest.mark.parametrize("h,w,L", [(150, 261, 3), (131, 9, 4), (64, 64, 6)])
+def test_zeta_normalisation_vs_oracle(dwt, scheme, wavelet, h, w, L):
+    """The paper's scaling step (DWT_NORM_ZETA: low-pass x zeta, high-pass
+    x 1/zeta per axis) against the oracle's, forward and inverse."""
+    x = inputs.uniform_image(h, w, seed=h * 31 + w + L)
+    ref = oracle.dwt2(x.astype(np.float64), OID[wavelet], L, norm=oracle.NORM_ZETA)
+    plan = dwt.Plan(w, h, wavelet, L, "f32", scheme=scheme)
+    dwt.dwt_plan_set_normalization(plan.handle, dwt.DWT_NORM_ZETA)
+    xd = torch.from_numpy(x).cuda()
+    c = torch.empty_like(xd)
+    y = torch.empty_like(xd)
+    plan.forward(xd, c)
+    plan.inverse(c, y)
+    torch.cuda.synchronize()
+    assert dwt.dwt_plan_device_status(plan.handle) == dwt.DWT_OK
+    plan.close()
+    assert np.abs(c.cpu().numpy() - ref).max() <= zeta_tol(ref)
+    assert np.abs(y.cpu().numpy() - x).max() <= 2 * TOL_F32
+
+
+def test_zeta_normalisation_in_a_batch(dwt):
+    """Batched requests of plans with the paper's scaling take the batch
+    kernel's runtime-coefficient kinds; each result matches the oracle."""
+    shapes = [(301, 257, "cdf97", 3), (128, 96, "cdf53", 2), (77, 130, "cdf97", 1)]
+    plans, xs, cs, refs = [], [], [], []
+    for h, w, wl, L in shapes:
+        x = inputs.uniform_image(h, w, seed=h + w)
+        p = dwt.Plan(w, h, wl, L, "f32")
+        dwt.dwt_plan_set_normalization(p.handle, dwt.DWT_NORM_ZETA)
+        plans.append(p)
+        xs.append(torch.from_numpy(x).cuda())
+        cs.append(torch.empty_like(xs[-1]))
+        refs.append(oracle.dwt2(x.astype(np.float64), OID[wl], L, norm=oracle.NORM_ZETA))
+    status = torch.zeros(len(shapes), dtype=torch.int32, device="cuda")
+    dwt.submit([p.request(x, c) for p, x, c in zip(plans, xs, cs)], status=status)
+    torch.cuda.synchronize()
+    assert int(status.abs().sum()) == 0
+    for c, ref in zip(cs, refs):
+        assert np.abs(c.cpu().numpy() - ref).max() <= zeta_tol(ref)
+    for p in plans:
+        p.close()
+
+
 def test_dd137_unsupported_combinations(dwt):
     p = dwt.dwt_plan_create(64, 64, dwt.DWT_DD137, 2, dwt.DWT_F32)
     for name in ("polyphase", "polyphase*", "convolution"):
