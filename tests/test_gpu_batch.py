@@ -204,5 +204,13 @@ def test_batch_rejections(dwt):
         dwt.submit([j1.request(), r2])
     assert e.value.status == dwt.DWT_EINVAL
     dwt.submit([])
+    # DD 13/7 has no batch kind: the whole call is refused, nothing runs
+    dd = dwt.Plan(64, 80, "dd137", 2, "f32")
+    x = torch.zeros((80, 64), device="cuda")
+    o = torch.empty_like(x)
+    with pytest.raises(dwt.DwtError) as e:
+        dwt.submit([j1.request(), dd.request(x, o)])
+    assert e.value.status == dwt.DWT_EUNSUPPORTED
+    dd.close()
     for j in (j1, j2):
         j.close()
