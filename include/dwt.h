@@ -196,10 +196,9 @@ dwt_status dwt2_inverse_host(dwt_plan plan, const void* h_coef, size_t coef_pitc
  * may be NULL) is cleared and then receives DWT_ETIMEOUT for any request
  * whose wait or copy gave up.  A plan only supplies parameters here and
  * may appear in any number of requests; outputs may not overlap each other
- * or any input (DWT_EINVAL).  Batches take CDF 5/3 and 9/7 in float32 and
- * float16 storage and reversible 5/3 in int32; a DD 13/7 plan makes the
- * whole call fail with DWT_EUNSUPPORTED before anything is queued (run
- * those with dwt2_forward / dwt2_inverse).  The call uploads its work list
+ * or any input (DWT_EINVAL).  Batches take every plan: CDF 5/3 and 9/7 in
+ * float32 and float16 storage, DD 13/7 in float32, reversible 5/3 in int32.
+ * The call uploads its work list
  * from a ring of page-locked buffers and may wait for the upload of the
  * batch that last used its slot, so it cannot be captured into a CUDA
  * graph. */

@@ -46,6 +46,10 @@ using R6 = FloatKind<W97, __half, false, false>;
 using R7 = FloatKind<W97, __half, true, false>;
 using R8 = FloatKind<W53, __half, false, false>;
 using R9 = FloatKind<W53, __half, true, false>;
+using D0 = FloatKind<WDD, float, false, true>;
+using D1 = FloatKind<WDD, float, true, true>;
+using D2 = FloatKind<WDD, float, false, false>;
+using D3 = FloatKind<WDD, float, true, false>;
 
 constexpr int cmax_bytes(int a, int b) { return a > b ? a : b; }
 // runtime kinds share their geometry with the static ones
@@ -53,12 +57,13 @@ constexpr int kStageStride =
     cmax_bytes(cmax_bytes(cmax_bytes(K0::STAGE_BYTES, K1::STAGE_BYTES), cmax_bytes(K2::STAGE_BYTES, K3::STAGE_BYTES)),
                cmax_bytes(cmax_bytes(K4::STAGE_BYTES, K5::STAGE_BYTES),
                           cmax_bytes(cmax_bytes(K6::STAGE_BYTES, K7::STAGE_BYTES),
-                                     cmax_bytes(K8::STAGE_BYTES, K9::STAGE_BYTES))));
+                                     cmax_bytes(cmax_bytes(K8::STAGE_BYTES, K9::STAGE_BYTES),
+                                                cmax_bytes(D0::STAGE_BYTES, D1::STAGE_BYTES)))));
 
 __constant__ ConvTaps kNoTaps;  // none of the batch kinds reads taps
 
 // One strip of one level.  Not inlined: each kind gets its own register
-// allocation instead of the union of all ten.
+// allocation instead of the union of all of them.
 template <class C>
 __device__ __noinline__ bool go(const BatchLevel& L, int cs, int rs, bool new_level, unsigned char* ring,
                                 uint64_t* bars, uint32_t& ctr) {
@@ -93,6 +98,10 @@ __device__ __forceinline__ bool dispatch(const BatchLevel& L, int cs, int rs, bo
     case BK_97_F16_INV_RT: return go<R7>(L, cs, rs, nl, ring, bars, ctr);
     case BK_53_F16_FWD_RT: return go<R8>(L, cs, rs, nl, ring, bars, ctr);
     case BK_53_F16_INV_RT: return go<R9>(L, cs, rs, nl, ring, bars, ctr);
+    case BK_DD_F32_FWD: return go<D0>(L, cs, rs, nl, ring, bars, ctr);
+    case BK_DD_F32_INV: return go<D1>(L, cs, rs, nl, ring, bars, ctr);
+    case BK_DD_F32_FWD_RT: return go<D2>(L, cs, rs, nl, ring, bars, ctr);
+    case BK_DD_F32_INV_RT: return go<D3>(L, cs, rs, nl, ring, bars, ctr);
   }
   return false;
 }
@@ -172,6 +181,10 @@ bool batch_kind_info(int kind, KernelInfo* k) {
     case BK_97_F16_INV_RT: kind_info<R7>(k); return true;
     case BK_53_F16_FWD_RT: kind_info<R8>(k); return true;
     case BK_53_F16_INV_RT: kind_info<R9>(k); return true;
+    case BK_DD_F32_FWD: kind_info<D0>(k); return true;
+    case BK_DD_F32_INV: kind_info<D1>(k); return true;
+    case BK_DD_F32_FWD_RT: kind_info<D2>(k); return true;
+    case BK_DD_F32_INV_RT: kind_info<D3>(k); return true;
   }
   return false;
 }

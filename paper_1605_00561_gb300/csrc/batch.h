@@ -7,7 +7,8 @@
 namespace dwt {
 
 // Kinds of level a batch can hold (scheme fixed per kind: Monolithic* for
-// float, the separable JPEG 2000 order for reversible 5/3).  The float kinds
+// float, including DD 13/7 in float32, the separable JPEG 2000 order for
+// reversible 5/3).  The float kinds
 // fold their coefficients in at compile time (JPEG 2000 normalisation, both
 // axes longer than one sample); the _RT kinds read them from the
 // descriptor and serve every other level.
@@ -15,7 +16,8 @@ enum BatchKind : int {
   BK_97_F32_FWD = 0, BK_97_F32_INV, BK_53_F32_FWD, BK_53_F32_INV, BK_53_I32_FWD, BK_53_I32_INV,
   BK_97_F16_FWD, BK_97_F16_INV, BK_53_F16_FWD, BK_53_F16_INV,
   BK_97_F32_FWD_RT, BK_97_F32_INV_RT, BK_53_F32_FWD_RT, BK_53_F32_INV_RT,
-  BK_97_F16_FWD_RT, BK_97_F16_INV_RT, BK_53_F16_FWD_RT, BK_53_F16_INV_RT, BK_COUNT
+  BK_97_F16_FWD_RT, BK_97_F16_INV_RT, BK_53_F16_FWD_RT, BK_53_F16_INV_RT,
+  BK_DD_F32_FWD, BK_DD_F32_INV, BK_DD_F32_FWD_RT, BK_DD_F32_INV_RT, BK_COUNT
 };
 
 // The kind that serves a level without compile-time coefficients.
@@ -29,6 +31,8 @@ inline int batch_runtime_kind(int kind) {
     case BK_97_F16_INV: return BK_97_F16_INV_RT;
     case BK_53_F16_FWD: return BK_53_F16_FWD_RT;
     case BK_53_F16_INV: return BK_53_F16_INV_RT;
+    case BK_DD_F32_FWD: return BK_DD_F32_FWD_RT;
+    case BK_DD_F32_INV: return BK_DD_F32_INV_RT;
     default: return kind;  // integer kinds take no float coefficients
   }
 }

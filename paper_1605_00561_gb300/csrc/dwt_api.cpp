@@ -898,6 +898,7 @@ int batch_kind(int wavelet, int dtype, bool inverse) {
   if (dtype == DWT_I32 && wavelet == DWT_CDF53) return BK_53_I32_FWD + inv;
   if (dtype == DWT_F16S && wavelet == DWT_CDF97) return BK_97_F16_FWD + inv;
   if (dtype == DWT_F16S && wavelet == DWT_CDF53) return BK_53_F16_FWD + inv;
+  if (dtype == DWT_F32 && wavelet == DWT_DD137) return BK_DD_F32_FWD + inv;
   return -1;
 }
 
