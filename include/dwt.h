@@ -232,8 +232,9 @@ dwt_status dwt_plan_read_profile(dwt_plan plan, dwt_kernel_stat* stats, int capa
 
 /* Run the autotuner for this plan now: time the forward transform of a
  * trial image (device memory allocated and freed here) for every scheme the
- * plan's wavelet and dtype support, then the strip height (6..24 rows) and
- * the ring depth (1..4 stages) for the fastest scheme.  The choice applies
+ * plan's wavelet and dtype support, each at its default strip height, then
+ * the strip height (6..48 rows) and the ring depth (1..4 stages) for the
+ * fastest scheme.  The choice applies
  * to this plan (the scheme if it is DWT_AUTO, the tile unless the caller set
  * one) and is appended to the cache file named by the environment variable
  * DWT_AUTOTUNE_CACHE (if set), which later plans of the same GPU, size,
