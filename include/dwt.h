@@ -97,9 +97,9 @@ typedef enum { DWT_NORM_JPEG2000 = 0, DWT_NORM_ZETA = 1 } dwt_norm;
  * and storage type.  Host-only: the plan's device memory (its status word
  * and the LL ping-pong scratch, about 3/8 w*h elements) is allocated by its
  * first single-image call, so plans used only in batches never touch
- * device memory and are cheap to create and destroy.  Errors: DWT_EINVAL for w < 1, h < 1,
- * levels < 0, levels above the number of halvings until both dimensions
- * are 1, or out == NULL; DWT_EUNSUPPORTED for DWT_I32 with a wavelet other
+ * device memory and are cheap to create and destroy.  Errors: DWT_EINVAL for
+ * w or h outside 1..2^28, levels < 0, levels above the number of halvings
+ * until both dimensions are 1, or out == NULL; DWT_EUNSUPPORTED for DWT_I32 with a wavelet other
  * than 5/3 and for DWT_DD137 with a storage type other than DWT_F32; DWT_ENOMEM; DWT_ECUDA. */
 dwt_status dwt_plan_create(int w, int h, dwt_wavelet wavelet, int levels, dwt_dtype dtype,
                            dwt_plan* out);
@@ -158,8 +158,8 @@ dwt_status dwt2_inverse(dwt_plan plan, const void* d_coef, size_t coef_pitch_byt
  * bytes, which every GPU that loads the library holds until the process
  * exits.  Images whose LL scratch (row pitch ceil(w/2) elements rounded up
  * to 128 bytes, times ceil(h/2) + ceil(h/4) rows; none for levels <= 1)
- * exceeds 32 MiB -- above about 4096 x 4096 float32 -- are rejected with
- * DWT_EINVAL.  The call makes no cudaMalloc, cudaFree or other allocating
+ * exceeds 32 MiB -- above about 4096 x 4096 float32 -- and sides outside
+ * 1..2^28 are rejected with DWT_EINVAL.  The call makes no cudaMalloc, cudaFree or other allocating
  * call.  The first call on each device looks up the array's device address
  * (once per device, with that device current); make that first call before
  * any stream capture.  All calls share the array and it keeps the previous

@@ -308,6 +308,10 @@ int encode_level_maps(TmaMaps* maps, int dtype, const LevelArgs& a, const Kernel
 
 size_t elem_size(int dtype) { return dtype == F16S ? 2 : 4; }
 
+// Largest side a plan accepts: quad, strip and row counts and the halvings
+// of a side stay far from int overflow.
+constexpr int kMaxSide = 1 << 28;
+
 // Quad rows per strip.  Strips of about ten rows keep several waves of
 // one-warp blocks in flight, so the block scheduler balances SMs that
 // progress at different rates, while the vertical halo re-reads hit L2
@@ -1211,7 +1215,7 @@ namespace dwt {
 dwt_status forward_on_scratch(int w, int h, int wavelet, int levels, int dtype, const void* src,
                               size_t src_pitch, void* dst, size_t dst_pitch, void* scratch,
                               size_t scratch_bytes, int* d_status, cudaStream_t s) {
-  if (w < 1 || h < 1 || levels < 0 || levels > 30) return DWT_EINVAL;
+  if (w < 1 || h < 1 || w > kMaxSide || h > kMaxSide || levels < 0 || levels > 30) return DWT_EINVAL;
   if (wavelet < 0 || wavelet > 2 || dtype < 0 || dtype > 2) return DWT_EINVAL;
   int Wk[32], Hk[32];
   Wk[0] = w;
@@ -1318,7 +1322,7 @@ dwt_status dwt_plan_create(int w, int h, dwt_wavelet wavelet, int levels, dwt_dt
                            dwt_plan* out) {
   if (!out) return DWT_EINVAL;
   *out = nullptr;
-  if (w < 1 || h < 1 || levels < 0) return DWT_EINVAL;
+  if (w < 1 || h < 1 || w > kMaxSide || h > kMaxSide || levels < 0) return DWT_EINVAL;
   if ((int)wavelet < 0 || (int)wavelet > 2 || (int)dtype < 0 || (int)dtype > 2) return DWT_EINVAL;
   int maxl = 0;
   for (int a = w, b = h; a > 1 || b > 1; a = (a + 1) / 2, b = (b + 1) / 2) ++maxl;

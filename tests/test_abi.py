@@ -49,6 +49,8 @@ def test_invalid_arguments_rejected_before_any_cuda_call(libdwt):
     lib = libdwt.lib()
     out = ctypes.c_void_p()
     assert lib.dwt_plan_create(0, 5, 0, 0, 0, ctypes.byref(out)) == libdwt.DWT_EINVAL
+    assert lib.dwt_plan_create((1 << 28) + 1, 5, 0, 0, 0, ctypes.byref(out)) == libdwt.DWT_EINVAL
+    assert lib.dwt_plan_create(5, 2 ** 31 - 1, 0, 0, 0, ctypes.byref(out)) == libdwt.DWT_EINVAL
     assert lib.dwt_plan_create(5, 5, 0, -1, 0, ctypes.byref(out)) == libdwt.DWT_EINVAL
     assert lib.dwt_plan_create(4, 4, 0, 3, 0, ctypes.byref(out)) == libdwt.DWT_EINVAL  # 2 halvings max
     assert lib.dwt_plan_create(4, 4, 7, 1, 0, ctypes.byref(out)) == libdwt.DWT_EINVAL
