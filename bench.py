@@ -177,6 +177,28 @@ def whole_job_rate(units_per_rank, world, ms_max):
     return world * units_per_rank / (ms_max / 1e3)
 
 
+def host_cpu():
+    """The host's core count and CPU model (from /proc/cpuinfo where it
+    names one), for the CPU baseline's record."""
+    import platform
+    model = ""
+    try:
+        with open("/proc/cpuinfo") as f:
+            info = f.read().splitlines()
+        for key in ("model name", "Model", "CPU part"):
+            for line in info:
+                if line.split(":")[0].strip() == key:
+                    model = line.split(":", 1)[1].strip()
+                    break
+            if model:
+                if key == "CPU part":
+                    model = f"{platform.machine()} CPU part {model}"
+                break
+    except OSError:
+        pass
+    return {"nproc": os.cpu_count(), "cpu": model or platform.machine()}
+
+
 def cpu_baseline_oracle(a, n=None, reps=2):
     """The oracle as it stands (single-threaded C, FP64) on host cores: the
     full workload image, forward then inverse, `reps` times (about 15 s)."""
@@ -232,7 +254,8 @@ def run_reference(a, rank, world):
         "steps": a.steps, "warmup": a.warmup, "ms_per_step": dt * 1e3 / a.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": workload_name(a)},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+                         "host": host_cpu()},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
 
@@ -816,7 +839,8 @@ def main():
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         v, dt, nn = cpu_baseline_oracle(a)
         cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"{nn}x{nn} forward + inverse, twice ({dt:.1f} s), FP64 C oracle, 1 thread"}
+               "sample": f"{nn}x{nn} forward + inverse, twice ({dt:.1f} s), FP64 C oracle, 1 thread",
+               "host": host_cpu()}
 
     if rank == 0:
         print(json.dumps({
