@@ -141,13 +141,15 @@ def test_dd137_unsupported_combinations(dwt):
         with pytest.raises(dwt.DwtError) as e:
             dwt.dwt_plan_set_scheme(p, dwt.SCHEMES[name])
         assert e.value.status == dwt.DWT_EUNSUPPORTED
-    # the batch kernel holds no DD 13/7 kind
-    x = torch.zeros(64, 64, device="cuda")
+    # batches run DD 13/7 plans with their Monolithic* kind
+    xh = inputs.uniform_image(64, 64, seed=5)
+    x = torch.from_numpy(xh).cuda()
     y = torch.empty_like(x)
     req = dwt.DwtRequest(p, x.data_ptr(), 256, y.data_ptr(), 256, 0)
-    with pytest.raises(dwt.DwtError) as e:
-        dwt.dwt_batch_submit([req])
-    assert e.value.status == dwt.DWT_EUNSUPPORTED
+    dwt.dwt_batch_submit([req])
+    torch.cuda.synchronize()
+    ref = oracle.dwt2(xh.astype(np.float64), oracle.DD137, 2)
+    assert np.abs(y.cpu().numpy() - ref).max() <= TOL_F32
     dwt.dwt_plan_destroy(p)
 
 
