@@ -811,21 +811,27 @@ def main():
         e2e_step(i)
     torch.cuda.synchronize()
     barrier()
+    # three windows of k2 steps; the line reports the median window (the
+    # host link's throughput moves by several percent from window to window)
     k2 = max(2, a.e2e_steps)
-    e0.record(streams[0])
-    streams[1].wait_event(e0)
-    for i in range(k2):
-        e2e_step(i)
-    done1 = torch.cuda.Event()
-    done1.record(streams[1])
-    streams[0].wait_event(done1)
-    e1.record(streams[0])
-    torch.cuda.synchronize()
-    ms2 = max_over_ranks(e0.elapsed_time(e1), world, "cuda")
+    windows = []
+    for _ in range(3):
+        e0.record(streams[0])
+        streams[1].wait_event(e0)
+        for i in range(k2):
+            e2e_step(i)
+        done1 = torch.cuda.Event()
+        done1.record(streams[1])
+        streams[0].wait_event(done1)
+        e1.record(streams[0])
+        torch.cuda.synchronize()
+        ms2 = max_over_ranks(e0.elapsed_time(e1), world, "cuda")
+        windows.append(whole_job_rate(2.0 * n * n * k2, world, ms2) / 1e9)
     assert float((yhs[0] - xh).abs().max()) < 0.05  # the data made the round trip
-    e2e = {"value": whole_job_rate(2.0 * n * n * k2, world, ms2) / 1e9, "unit": UNIT,
+    e2e = {"value": statistics.median(windows), "unit": UNIT,
            "h2d_bytes_per_step": 2 * n * n * 4, "d2h_bytes_per_step": 2 * n * n * 4,
-           "pipelining": "two plans on two streams, steps alternating"}
+           "pipelining": "two plans on two streams, steps alternating",
+           "windows": windows, "steps_per_window": k2}
     # the host link bounds this number: plain copies of one image buffer
     # (pinned host memory), each direction alone and both at once
     link = host_link_gbs(torch, x, xh, chs[1], streams)
