@@ -108,7 +108,7 @@ class _Batch:
 
 class Server:
     def __init__(self, budget_bytes: Optional[int] = None, reserve_bytes: int = 4 << 30,
-                 max_inflight: int = 3, max_batch: int = 1024, per_request: bool = False,
+                 max_inflight: int = 8, max_batch: int = 1024, per_request: bool = False,
                  plan_cache: int = 4096, device: Optional[int] = None,
                  on_done: Optional[Callable[[Request], None]] = None):
         if not torch.cuda.is_available():
