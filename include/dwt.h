@@ -95,8 +95,9 @@ typedef enum { DWT_NORM_JPEG2000 = 0, DWT_NORM_ZETA = 1 } dwt_norm;
 
 /* Create a plan for a w x h image, `levels` levels (0 = plain copy), wavelet
  * and storage type.  Host-only: the plan's device memory (its status word
- * and the LL ping-pong scratch, about 3/8 w*h elements) is allocated by its
- * first single-image call, so plans used only in batches never touch
+ * and one LL buffer per level after the first, each of ceil(W_k/2) x
+ * ceil(H_k/2) elements with rows at a 128-byte pitch, about w*h/3 elements
+ * in all) is allocated by its first single-image call, so plans used only in batches never touch
  * device memory and are cheap to create and destroy.  Errors: DWT_EINVAL for
  * w or h outside 1..2^28, levels < 0, levels above the number of halvings
  * until both dimensions are 1, or out == NULL; DWT_EUNSUPPORTED for DWT_I32 with a wavelet other

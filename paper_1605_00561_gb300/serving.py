@@ -85,17 +85,23 @@ class Request:
 
 def request_bytes(r: Request) -> int:
     """Device bytes a request holds while in flight: its output plane (rows
-    at a 128-byte pitch) and the LL ping-pong scratch of its batch work area
-    (rows of ceil(w/2) elements at a 128-byte pitch, ceil(h/2) + ceil(h/4)
-    of them)."""
+    at a 128-byte pitch) and the LL buffers of its batch work area, one per
+    level after the first (ceil(W_k/2) x ceil(H_k/2) elements, rows at a
+    128-byte pitch, each buffer starting on a 256-byte boundary), plus a
+    bound on its share of the work list: per level a 1 KiB descriptor, an
+    8-byte item per strip and 12 bytes per row of strips, for strips of at
+    least 2 quadruple rows and 120 columns."""
     es = ELEM[r.dtype]
-    out = out_pitch(r.w, r.dtype) * r.h
-    if r.levels < 2:
-        return out
-    w1, h1 = (r.w + 1) // 2, (r.h + 1) // 2
-    h2 = (h1 + 1) // 2
-    pitch = (w1 * es + 127) // 128 * 128
-    return out + pitch * (h1 + h2) + 1024
+    total = out_pitch(r.w, r.dtype) * r.h
+    w, h = r.w, r.h
+    for k in range(r.levels):
+        cw, ch = (w + 1) // 2, (h + 1) // 2
+        nrs = (ch + 1) // 2
+        total += 1024 + 8 * ((cw + 119) // 120) * nrs + 12 * nrs
+        if k + 1 < r.levels:
+            total += ((cw * es + 127) // 128 * 128 * ch + 255) // 256 * 256
+        w, h = cw, ch
+    return total
 
 
 @dataclass
