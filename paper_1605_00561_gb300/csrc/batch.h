@@ -71,6 +71,8 @@ struct BatchParams {
 bool batch_kind_info(int kind, KernelInfo* k);
 size_t batch_smem_bytes();
 const void* batch_kernel_fn();
-cudaError_t launch_batch(const BatchParams& p, int blocks, cudaStream_t s);
+// with_dd: the batch holds DD 13/7 requests (the kernel that dispatches
+// their kinds as well)
+cudaError_t launch_batch(const BatchParams& p, int blocks, bool with_dd, cudaStream_t s);
 
 }  // namespace dwt

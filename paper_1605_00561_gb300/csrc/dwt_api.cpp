@@ -957,6 +957,7 @@ dwt_status batch_submit(const dwt_request* reqs, int n, cudaStream_t s, int* d_s
   if (device < 0 || device >= 64) return DWT_EUNSUPPORTED;
   std::vector<int> kinds(n);
   int maxl = 0;
+  bool with_dd = false;
   for (int i = 0; i < n; ++i) {
     const dwt_plan_s* p = reqs[i].plan;
     if (p->device != device) return DWT_EINVAL;
@@ -964,6 +965,7 @@ dwt_status batch_submit(const dwt_request* reqs, int n, cudaStream_t s, int* d_s
     if (chk != DWT_OK) return chk;
     kinds[i] = batch_kind(p->wavelet, p->dtype, reqs[i].inverse != 0);
     if (kinds[i] < 0) return DWT_EUNSUPPORTED;
+    with_dd = with_dd || p->wavelet == DWT_DD137;
     maxl = std::max(maxl, p->levels);
   }
   // images may not share memory with each other either: no output range
@@ -1183,7 +1185,7 @@ dwt_status batch_submit(const dwt_request* reqs, int n, cudaStream_t s, int* d_s
     bp.head = head;
     bp.row_done = row_done;
     bp.req_status = status;
-    e = launch_batch(bp, (int)std::min<size_t>((size_t)resident, nitems), s);
+    e = launch_batch(bp, (int)std::min<size_t>((size_t)resident, nitems), with_dd, s);
   }
   const cudaError_t ef = cudaFreeAsync(block, s);
   if (e == cudaSuccess) e = ef;
