@@ -487,8 +487,10 @@ def run_batch(a):
     def batch_fwd():
         dwt.submit(fwd, status=status)
 
+    # the library's own batch tile (no plan has a tile set), then the
     # strip-height autotuner: coordinate descent over three area classes,
     # timing the whole batch for each candidate
+    t_fwd_default = time_back_to_back(torch, batch_fwd, max(3, a.steps // 2), warm=a.warmup)
     areas = sorted(w * h for w, h, _ in shapes)
     cuts = [areas[len(areas) // 3], areas[2 * len(areas) // 3]]
     cls = [0 if w * h <= cuts[0] else 1 if w * h <= cuts[1] else 2 for w, h, _ in shapes]
@@ -594,6 +596,7 @@ def run_batch(a):
         "timing": "back-to-back batches (device time per batch; host planning overlapped); "
                   "latency = one batch from the call to completion",
         "batch_fwd_us": t_fwd, "batch_inv_us": t_inv, "batch_fwd_latency_us": lat_fwd,
+        "batch_fwd_us_library_default_tile": t_fwd_default,
         "host_submit_ms": statistics.median(host),
         "batch_fwd_gpx_s": pixels / t_fwd / 1e3, "batch_inv_gpx_s": pixels / t_inv / 1e3,
         "batch_fwd_hbm_frac": ab / (t_fwd * 1e-6) / 1e9 / peak, "peak_gbs": peak,
