@@ -189,7 +189,9 @@ dwt_status dwt2_inverse_host(dwt_plan plan, const void* h_coef, size_t coef_pitc
  * the same image is done.  The scheme is fixed per dtype whatever the plan
  * selects: Monolithic* (Sec. 4) for float32 and float16 storage, the
  * separable JPEG 2000 lifting order for reversible int32 5/3; the plans'
- * normalisation and strip height apply.  Each request's LL scratch and the
+ * normalisation applies, and their tile where the caller set one with
+ * dwt_plan_set_tile (otherwise batches take 48-row strips and a 4-stage
+ * ring, which suit the persistent kernel).  Each request's LL scratch and the
  * work list live in one work area that the call takes from a
  * library-owned stream-ordered memory pool and returns at the end of the
  * launch (the pool keeps its peak size for later batches), so batches
