@@ -202,6 +202,29 @@ def test_tall_strip_schemes_8192_full_compare(dwt, scheme, wavelet):
     assert np.abs(y - x).max() <= TOL_ROUND_TRIP
 
 
+@pytest.mark.parametrize("scheme", ["monolithic*", "iwahashi*", "convolution"])
+@pytest.mark.parametrize("h,w,L", [(131072, 3, 3), (3, 131072, 3), (70001, 1, 4), (1, 70001, 4)])
+def test_extreme_aspect_ratios(dwt, scheme, h, w, L):
+    """Lines and near-lines: one column of strips with thousands of rows of
+    strips (for the 32-row Iwahashi* strips more than a wave, so their rows
+    are dealt), one row of strips with thousands of columns, and length-1
+    axes."""
+    x = inputs.uniform_image(h, w, seed=h + w + L)
+    ref = oracle.dwt2(x.astype(np.float64), oracle.CDF97, L)
+    c, y, _ = run_fwd_inv(dwt, x, "cdf97", L, "f32", scheme)
+    assert np.abs(c - ref).max() <= TOL_F32
+    assert np.abs(y - x).max() <= TOL_ROUND_TRIP
+
+
+@pytest.mark.parametrize("h,w", [(131072, 3), (3, 131072), (70001, 1)])
+def test_int53_extreme_aspect_ratios_bit_exact(dwt, h, w):
+    x = inputs.int12_image(h, w, seed=11)
+    ref = oracle.dwt2_int(x, 3)
+    c, y, _ = run_fwd_inv(dwt, x, "cdf53", 3, "i32", "sweldens")
+    assert np.array_equal(c, ref)
+    assert np.array_equal(y, x)
+
+
 @pytest.mark.parametrize("h,w", [(4096, 4096), (3333, 5001)])
 def test_int53_config_sizes_bit_exact(dwt, h, w):
     x = inputs.int12_image(h, w, seed=7)
