@@ -104,6 +104,8 @@ MIX = [  # h, w, wavelet, levels, dtype, inverse
     (261, 150, "dd137", 2, "f32", True),
     (1, 37, "dd137", 2, "f32", False),
     (600, 700, "dd137", 4, "f32", False),
+    (65536, 3, "cdf97", 3, "f32", False),
+    (3, 65536, "cdf53", 3, "i32", True),
 ]
 
 
