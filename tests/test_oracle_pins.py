@@ -112,11 +112,27 @@ SIZES = [(1, 1), (1, 4), (4, 1), (2, 2), (2, 5), (3, 7), (5, 6), (7, 9), (8, 8),
 # CDF 5/3: exact
 # ----------------------------------------------------------------------------
 
+def paper_pair(golden, wavelet):
+    """(P, U) of `wavelet` as the paper prints them (Sec. 5), converted from
+    powers of z to quad offsets (z^e reads offset -e)."""
+    ops = {"P": {}, "U": {}}
+    for wl, op, e, c in golden("paper_lifting_pairs.txt"):
+        if wl == wavelet:
+            ops[op][-int(e)] = Fraction(c)
+    return ops["P"], ops["U"]
+
+
 def test_cdf53_filters_follow_from_paper_lifting(golden):
     lo_g, hi_g = golden_filters(golden, "cdf53_filters.txt")
-    lo, hi = compose_1d(sa.cdf53())
+    lo, hi = compose_1d([paper_pair(golden, "CDF 5/3")])
     assert lo == lo_g
     assert hi == hi_g
+
+
+def test_scheme_algebra_pairs_are_the_papers(golden):
+    # the step matrices of oracle/scheme_algebra.py are built from these pairs
+    assert sa.cdf53() == [paper_pair(golden, "CDF 5/3")]
+    assert sa.dd137() == [paper_pair(golden, "DD 13/7")]
 
 
 @pytest.mark.parametrize("h,w", SIZES)
@@ -173,8 +189,8 @@ def test_cdf97_bruteforce_convolution(h, w):
 
 
 @pytest.mark.parametrize("h,w", [(2, 9), (6, 5), (9, 9)])
-def test_dd137_bruteforce_convolution(h, w):
-    lo, hi = compose_1d(sa.dd137())
+def test_dd137_bruteforce_convolution(golden, h, w):
+    lo, hi = compose_1d([paper_pair(golden, "DD 13/7")])
     rng = np.random.default_rng(300 + h * w)
     x = rng.integers(0, 256, (h, w))
     ref = brute_force_level([[Fraction(int(v)) for v in row] for row in x], lo, hi)
@@ -275,15 +291,99 @@ def test_integer_linear_ramps_and_constants_exact():
     assert np.all(yc[:3, :3] == 1234) and np.count_nonzero(yc) == 9
 
 
-def test_integer_close_to_float_53():
-    # with no rounding the reversible 5/3 is the float 5/3 (JPEG 2000
-    # normalisation leaves 5/3 unscaled); floors move each band by at most
-    # a couple of units per level
-    x = np.random.default_rng(5).integers(0, 4096, (40, 36))
-    yi = oracle.dwt2_int(x, 1)
-    yf = oracle.dwt2(x.astype(float), oracle.CDF53, 1)
-    assert np.abs(yi - yf).max() <= 2.0
-    assert np.abs(yi - yf).max() > 0
+def _ints(field):
+    return [int(v) for v in field.split()]
+
+
+def test_integer_golden_lines(golden):
+    # hand-derived JPEG 2000 reversible 5/3 lines (tests/golden/int53_vectors.txt)
+    rows = [r for r in golden("int53_vectors.txt") if len(r) == 3]
+    assert len(rows) == 5
+    for name, x, y in rows:
+        got = oracle.dwt1_int(_ints(x))
+        assert got.tolist() == _ints(y), name
+        assert oracle.dwt1_int(got, inverse=True).tolist() == _ints(x), name
+
+
+def test_integer_golden_image(golden):
+    (name, h, w, L, x, y), = [r for r in golden("int53_vectors.txt") if len(r) == 6]
+    h, w, L = int(h), int(w), int(L)
+    x = np.array(_ints(x)).reshape(h, w)
+    want = np.array(_ints(y)).reshape(h, w)
+    got = oracle.dwt2_int(x, L)
+    assert np.array_equal(got, want), name
+    assert np.array_equal(oracle.dwt2_int(got, L, inverse=True), x)
+
+
+def _lift53_int_variant(x, plus2=True, predict="floor", update="floor"):
+    """The test's own statement of the reversible 5/3 forward line, with a
+    rounding mistake planted on request: the update without its +2, the
+    predict rounding half up (floor((a + b + 1)/2)) or truncating toward
+    zero, the update truncating toward zero."""
+    def trunc_div(a, b):
+        q = abs(a) // b
+        return q if a >= 0 else -q
+
+    n, t = len(x), list(x)
+    if n == 1:
+        return t
+    for i in range(1, n, 2):
+        a = t[wss(i - 1, n)] + t[wss(i + 1, n)]
+        t[i] -= {"floor": a // 2, "half_up": (a + 1) // 2, "trunc": trunc_div(a, 2)}[predict]
+    for i in range(0, n, 2):
+        a = t[wss(i - 1, n)] + t[wss(i + 1, n)] + (2 if plus2 else 0)
+        t[i] += a // 4 if update == "floor" else trunc_div(a, 4)
+    return t[0::2] + t[1::2]
+
+
+@pytest.mark.parametrize("mistake", [dict(plus2=False), dict(predict="half_up"), dict(predict="trunc"),
+                                     dict(update="trunc")])
+def test_integer_golden_lines_catch_rounding_mistakes(golden, mistake):
+    # the vectors are not vacuous: each plausible rounding mistake changes
+    # the result of at least one golden line (the unplanted statement
+    # reproduces all of them)
+    rows = [r for r in golden("int53_vectors.txt") if len(r) == 3]
+    assert all(_lift53_int_variant(_ints(x)) == _ints(y) for _, x, y in rows)
+    assert any(_lift53_int_variant(_ints(x), **mistake) != _ints(y) for _, x, y in rows)
+
+
+def test_integer_1d_rounding_error_intervals():
+    # Float 5/3 (JPEG 2000 normalisation leaves it unscaled) is the reversible
+    # transform without its floors.  From the two equations: the high-pass
+    # error is (a + b)/2 - floor((a + b)/2), which is 0 or 1/2; the low-pass
+    # error is floor((D + 2)/4) - D/4 + (e1 + e2)/4 with D = d1 + d2 and e1,
+    # e2 the two high-pass errors, which lies in [-1/4, 3/4].  A dropped +2
+    # moves the low band to [-3/4, 1/4], half-up rounding the high band to
+    # [-1/2, 0]: random lines hit those outside the intervals.
+    rng = np.random.default_rng(17)
+    for n in (2, 3, 8, 9, 64, 65):
+        for _ in range(200 // n + 5):
+            x = rng.integers(-4096, 4096, n)
+            ei = oracle.dwt1_int(x) - oracle.dwt1(x.astype(float), oracle.CDF53)
+            nlo = (n + 1) // 2
+            lo, hi = ei[:nlo], ei[nlo:]
+            assert np.all((hi == 0) | (hi == 0.5))
+            assert lo.min() >= -0.25 and lo.max() <= 0.75
+
+
+def test_integer_2d_rounding_error_intervals():
+    # One 2-D level: the column pass leaves errors in [-1/4, 3/4] (low rows)
+    # and [0, 1/2] (high rows); the row pass adds its own and maps the column
+    # errors through the float filters.  The high-pass filter (-1/2, 1, -1/2)
+    # maps [a, b] to [-(b - a), b - a]; the low-pass filter (-1/8, 1/4, 3/4,
+    # 1/4, -1/8; positive taps 5/4, negative -1/4) maps [a, b] to
+    # [5a/4 - b/4, 5b/4 - a/4].  So LL in [-3/4, 7/4], HL in [-1, 3/2], LH in
+    # [-3/8, 11/8], HH in [-1/2, 1].
+    rng = np.random.default_rng(5)
+    for h, w in ((40, 36), (33, 47), (2, 9), (64, 64)):
+        x = rng.integers(0, 4096, (h, w))
+        e = oracle.dwt2_int(x, 1) - oracle.dwt2(x.astype(float), oracle.CDF53, 1)
+        ch, cw = (h + 1) // 2, (w + 1) // 2
+        bands = {"LL": (e[:ch, :cw], -0.75, 1.75), "HL": (e[:ch, cw:], -1.0, 1.5),
+                 "LH": (e[ch:, :cw], -0.375, 1.375), "HH": (e[ch:, cw:], -0.5, 1.0)}
+        for name, (b, lo, hi) in bands.items():
+            assert b.min() >= lo and b.max() <= hi, (name, h, w, b.min(), b.max())
+        assert np.abs(e).max() > 0
 
 
 def test_integer_range_12bit_five_levels_and_overflow_detected():
