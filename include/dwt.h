@@ -147,28 +147,39 @@ dwt_status dwt2_forward(dwt_plan plan, const void* d_in, size_t in_pitch_bytes, 
 dwt_status dwt2_inverse(dwt_plan plan, const void* d_coef, size_t coef_pitch_bytes, void* d_out,
                         size_t out_pitch_bytes, dwt_stream stream);
 
-/* Forward transform for callers that cannot allocate device memory: code
- * that runs while a CUDA graph is being captured, real-time loops that must
- * not call cudaMalloc (it can synchronise the device and take unbounded
- * time), and host frameworks that own every allocation themselves.  The
- * paper has no counterpart; it is the plan-free twin of dwt2_forward with
- * the default scheme (Monolithic* for float, the separable JPEG 2000 order
- * for int32) and default tile.  The caller passes the input and output as
- * for dwt2_forward; the LL scratch of the pyramid and a device status word
- * live in one file-scope device array of this library, 32 MiB plus 256
- * bytes, which every GPU that loads the library holds until the process
- * exits.  Images whose LL scratch (row pitch ceil(w/2) elements rounded up
- * to 128 bytes, times ceil(h/2) + ceil(h/4) rows; none for levels <= 1)
- * exceeds 32 MiB -- above about 4096 x 4096 float32 -- and sides outside
- * 1..2^28 are rejected with DWT_EINVAL.  The call makes no cudaMalloc, cudaFree or other allocating
- * call.  The first call on each device looks up the array's device address
- * (once per device, with that device current); make that first call before
- * any stream capture.  All calls share the array and it keeps the previous
- * call's contents: calls that overlap on the GPU (other streams, or another
- * thread) race on it, so serialise them. */
+/* Forward transform for callers that cannot allocate device memory: a
+ * real-time loop that must not call cudaMalloc (it can synchronise the
+ * device and take unbounded time), an embedded or plug-in caller whose host
+ * application owns every device allocation, or a memory-capped process
+ * that has already spent its budget.  The paper has no counterpart; it is
+ * the plan-free twin of dwt2_forward with the default scheme (Monolithic*
+ * for float, the separable JPEG 2000 order for int32) and the tile a fresh
+ * plan takes.  The caller passes the input and output as for dwt2_forward;
+ * the LL scratch of the pyramid and a device status word live in one
+ * file-scope device array of this library, 32 MiB plus 256 bytes, which
+ * every GPU that loads the library holds until the process exits.  Images
+ * whose LL scratch (row pitch ceil(w/2) elements rounded up to 128 bytes,
+ * times ceil(h/2) + ceil(h/4) rows; none for levels <= 1) exceeds 32 MiB --
+ * above about 4096 x 4096 float32 -- and sides outside 1..2^28 are rejected
+ * with DWT_EINVAL.  The call makes no cudaMalloc, cudaFree or other
+ * allocating call.  The first call on each device looks up the array's
+ * device address (once per device, with that device current); make that
+ * first call before any stream capture.  All calls share the array and it
+ * keeps the previous call's contents: calls that overlap on the GPU (other
+ * streams, or another thread) race on it, so serialise them.  A bounded
+ * device wait that runs out raises the array's status word, which
+ * dwt_noalloc_device_status reads. */
 dwt_status dwt2_forward_noalloc(int w, int h, dwt_wavelet wavelet, int levels, dwt_dtype dtype,
                                 const void* d_in, size_t in_pitch_bytes, void* d_out,
                                 size_t out_pitch_bytes, dwt_stream stream);
+
+/* Synchronise `stream` (the stream of the dwt2_forward_noalloc calls) and
+ * report whether a bounded device wait of any such call on the current
+ * device ran out since the previous query: DWT_ETIMEOUT (the output of the
+ * call concerned is incomplete) or DWT_OK; the word is cleared.  Reads one
+ * device word with a copy into host memory; allocates nothing.  DWT_ECUDA
+ * if a CUDA call fails. */
+dwt_status dwt_noalloc_device_status(dwt_stream stream);
 
 /* Same transforms with HOST buffers: the call copies the input to device
  * staging owned by the plan, transforms it, and copies the result back into
@@ -219,6 +230,37 @@ dwt_status dwt_batch_submit(const dwt_request* reqs, int n, dwt_stream stream, i
 /* Synchronise with the plan's last stream and report device-side failures
  * of its calls since the previous query (DWT_OK or DWT_ETIMEOUT). */
 dwt_status dwt_plan_device_status(dwt_plan plan);
+
+/* Limits of the kernels' bounded device waits, for launches made after the
+ * call (process-wide): ring_probes bounds the wait for a row chunk's load
+ * (mbarrier probes), dep_spins the wait of a batch strip for the rows it
+ * reads and of an injected hold (polls a short sleep apart).  0 restores a
+ * default (2^24 probes, 2^22 polls: seconds at most).  A wait that runs out
+ * sets the status word that dwt_plan_device_status,
+ * dwt_noalloc_device_status or a batch's status array report. */
+dwt_status dwt_set_wait_limits(unsigned int ring_probes, unsigned int dep_spins);
+
+/* Host-side failure injection, for tests of the error paths (nothing here
+ * faults or hangs the GPU).  Each kind lets `skip` events pass and then
+ * acts on the next `count`; DWT_INJECT_NONE clears every kind.
+ *   DWT_INJECT_ENOMEM:    a device or page-locked allocation of the library
+ *                         fails as cudaErrorMemoryAllocation would.
+ *   DWT_INJECT_HOLD:      the first strip of a single-image level launch
+ *                         (plan or no-alloc call) waits, bounded by
+ *                         dep_spins, on a device flag that nothing sets, so
+ *                         that the wait runs out and reports DWT_ETIMEOUT.
+ *   DWT_INJECT_BATCH_DEP: in a batch, the second level of request 0 waits
+ *                         for one more finished strip per row than its rows
+ *                         have, a count nothing reaches; the request's
+ *                         status slot receives DWT_ETIMEOUT.
+ * Errors: DWT_EINVAL for an unknown kind or negative counts. */
+typedef enum {
+  DWT_INJECT_NONE = 0,
+  DWT_INJECT_ENOMEM = 1,
+  DWT_INJECT_HOLD = 2,
+  DWT_INJECT_BATCH_DEP = 3
+} dwt_injection;
+dwt_status dwt_debug_inject(dwt_injection what, int skip, int count);
 
 /* Per-kernel timing of a plan's calls, for measurement.  When enabled, each
  * launch is bracketed by CUDA events on the launching stream; reading the

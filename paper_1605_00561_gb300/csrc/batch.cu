@@ -141,7 +141,7 @@ __global__ void __launch_bounds__(32, 12) batch_kernel(const __grid_constant__ B
     bool ok = true;
     if (L.dep_row_base >= 0) {
       const int2 d = P.row_deps[L.row_base + rs];
-      ok = wait_rows(P.row_done + L.dep_row_base, d.x, d.y, L.dep_ncs);
+      ok = wait_rows(P.row_done + L.dep_row_base, d.x, d.y, L.dep_ncs, L.a.spins);
     }
     if (ok) ok = dispatch<WITH_DD>(L, cs, rs, item.level != fenced, smem_raw, bars, chunk_ctr);
     fenced = item.level;

@@ -48,7 +48,7 @@ struct alignas(64) BatchLevel {
   int request;
   int row_base;      // index of this level's strip row 0 in the row arrays
   int dep_row_base;  // the same for the level whose output it reads, or -1
-  int dep_ncs;       // column strips per row of that level
+  int dep_ncs;       // column strips per row of that level: the count a row of it waits for
 };
 
 struct BatchItem {

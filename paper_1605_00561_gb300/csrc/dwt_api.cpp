@@ -6,6 +6,7 @@
 #include "dwt.h"
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -221,16 +222,34 @@ struct Occ {
   int sms = 0;
   int per_sm = 0;
 };
+
+// Occupancy cache: a fixed open-addressing table (no heap allocation, so
+// the entry point that allocates nothing can use it too).  When it is full,
+// further keys are computed on every call instead of cached.
+struct OccEntry {
+  const void* fn;
+  int device;
+  size_t smem;
+  Occ occ;
+};
+constexpr int kOccSlots = 1024;
 std::mutex g_occ_mu;
-std::map<std::tuple<const void*, int, size_t>, Occ> g_occ;
+OccEntry g_occ[kOccSlots];
 
 // Resident blocks of one warp for kernel `fn` with `smem` bytes of dynamic
 // shared memory per block.
 Occ occupancy(const void* fn, size_t smem, int device) {
   std::lock_guard<std::mutex> lk(g_occ_mu);
-  auto key = std::make_tuple(fn, device, smem);
-  auto it = g_occ.find(key);
-  if (it != g_occ.end()) return it->second;
+  const size_t hsh = (reinterpret_cast<uintptr_t>(fn) >> 4) * 31u + (size_t)device * 131u + smem;
+  int free_slot = -1;
+  for (int i = 0; i < 16; ++i) {
+    OccEntry& e = g_occ[(hsh + i) % kOccSlots];
+    if (e.fn == fn && e.device == device && e.smem == smem) return e.occ;
+    if (!e.fn) {
+      free_slot = (int)((hsh + i) % kOccSlots);
+      break;
+    }
+  }
   Occ o;
   cudaDeviceGetAttribute(&o.sms, cudaDevAttrMultiProcessorCount, device);
   int optin = 0;
@@ -240,8 +259,57 @@ Occ occupancy(const void* fn, size_t smem, int device) {
     o.per_sm = 1;
   o.sms = std::max(o.sms, 1);
   o.per_sm = std::max(o.per_sm, 1);
-  g_occ[key] = o;
+  if (free_slot >= 0) g_occ[free_slot] = OccEntry{fn, device, smem, o};
   return o;
+}
+
+// ---------------------------------------------------------------------------
+// Wait limits and failure injection
+// ---------------------------------------------------------------------------
+std::atomic<uint32_t> g_ring_probes{kDefaultRingProbes};
+std::atomic<uint32_t> g_dep_spins{kDefaultDepSpins};
+
+// Host-side failure injection for tests of the error paths (dwt_debug_inject):
+// each kind lets `skip` events pass, then acts on the next `count`.
+struct Injection {
+  int skip = 0, count = 0;
+};
+std::mutex g_inject_mu;
+Injection g_inject[4];
+
+bool injected(int what) {
+  std::lock_guard<std::mutex> lk(g_inject_mu);
+  Injection& j = g_inject[what];
+  if (j.count <= 0) return false;
+  if (j.skip > 0) {
+    --j.skip;
+    return false;
+  }
+  --j.count;
+  return true;
+}
+
+// Every device or page-locked allocation of the library goes through these,
+// so that an injected allocation failure reaches each of them.
+cudaError_t dev_malloc(void** p, size_t n) {
+  if (injected(DWT_INJECT_ENOMEM)) return cudaErrorMemoryAllocation;
+  return cudaMalloc(p, n);
+}
+cudaError_t host_malloc(void** p, size_t n) {
+  if (injected(DWT_INJECT_ENOMEM)) return cudaErrorMemoryAllocation;
+  return cudaMallocHost(p, n);
+}
+cudaError_t pool_malloc(void** p, size_t n, cudaMemPool_t pool, cudaStream_t s) {
+  if (injected(DWT_INJECT_ENOMEM)) return cudaErrorMemoryAllocation;
+  return cudaMallocFromPoolAsync(p, n, pool, s);
+}
+
+// The wait limits and the injected hold of a single-image launch; `flag` is
+// a device word that nothing sets.
+void set_waits(LevelArgs& a, const int* flag) {
+  a.probes = g_ring_probes.load();
+  a.spins = g_dep_spins.load();
+  a.hold = injected(DWT_INJECT_HOLD) ? flag : nullptr;
 }
 Occ occupancy(const KernelInfo& ki, int device) { return occupancy(ki.fn, ki.smem_bytes, device); }
 
@@ -586,25 +654,31 @@ size_t smem_with_stages(const KernelInfo& ki, int info_stages, int nstages) {
   return (ki.smem_bytes - bars) / info_stages * nstages + bars;
 }
 
+// The tile a single-image launch uses: device, ring depth and strip height
+// (0: the default of the scheme).
+struct Tile {
+  int device, nstages, strip_rows;
+};
+
 // Strips of one level: column strips, strip height, strip rows and ring
 // depth, for the kernel of `key`.
-dwt_status level_geometry(const dwt_plan_s* p, const LaunchKey& key, LevelArgs& a, KernelInfo& ki) {
-  if (!find_kernel(key, p->nstages, &ki)) return DWT_EUNSUPPORTED;
-  const Occ oc = occupancy(ki, p->device);
+dwt_status level_geometry(const Tile& t, const LaunchKey& key, LevelArgs& a, KernelInfo& ki) {
+  if (!find_kernel(key, t.nstages, &ki)) return DWT_EUNSUPPORTED;
+  const Occ oc = occupancy(ki, t.device);
   const int cap = oc.sms * oc.per_sm;
   // one strip per resident warp when the level is large enough: a single
   // wave, with strips as tall as that allows (less vertical halo)
   a.ncs = (a.cw + ki.uq - 1) / ki.uq;
-  const int target = p->strip_rows > 0 ? p->strip_rows : default_strip_rows(key.scheme, key.wavelet);
+  const int target = t.strip_rows > 0 ? t.strip_rows : default_strip_rows(key.scheme, key.wavelet);
   a.T = strip_height(target, a.ch, a.ncs, cap, ki.up + ki.down, chunk_rows(ki));
   a.nrs = (a.ch + a.T - 1) / a.T;
   a.wave_rows = wave_rows(a, cap);
   // a level that does not fill the GPU once is latency-bound: a deeper
   // ring lets each (short) strip issue all its chunk loads at once, as long
   // as the level still fits one wave with the larger shared-memory ring
-  a.nstages = p->nstages;
-  if (p->nstages < kMaxStages && (long long)a.ncs * a.nrs < cap) {
-    const Occ deep = occupancy(ki.fn, smem_with_stages(ki, p->nstages, kMaxStages), p->device);
+  a.nstages = t.nstages;
+  if (t.nstages < kMaxStages && (long long)a.ncs * a.nrs < cap) {
+    const Occ deep = occupancy(ki.fn, smem_with_stages(ki, t.nstages, kMaxStages), t.device);
     if ((long long)a.ncs * a.nrs <= (long long)deep.sms * deep.per_sm) a.nstages = kMaxStages;
   }
   return DWT_OK;
@@ -614,9 +688,10 @@ dwt_status level_geometry(const dwt_plan_s* p, const LaunchKey& key, LevelArgs& 
 dwt_status launch(dwt_plan_s* p, const LaunchKey& key, LevelArgs& a, const Coefs& cf,
                   const ConvTaps& ct, cudaStream_t s, const char* slot) {
   KernelInfo ki{};
-  const dwt_status g = level_geometry(p, key, a, ki);
+  const dwt_status g = level_geometry(Tile{p->device, p->nstages, p->strip_rows}, key, a, ki);
   if (g != DWT_OK) return g;
   a.status = p->d_status;
+  set_waits(a, p->d_status + 1);
 
   TmaMaps maps;
   a.src_tma = encode_level_maps(&maps, p->dtype, a, ki, p->es);
@@ -650,7 +725,7 @@ void level_dims(const dwt_plan_s* p, int k, LevelArgs& a) {
 dwt_status ensure_tmp(dwt_plan_s* p) {
   if (p->tmp) return DWT_OK;
   p->tmp_pitch = round_up((size_t)p->w * p->es, 128);
-  return from_cuda(cudaMalloc(&p->tmp, p->tmp_pitch * p->h));
+  return from_cuda(dev_malloc(&p->tmp, p->tmp_pitch * p->h));
 }
 
 // Which strip rows of level d (the level whose output level a reads) each
@@ -758,11 +833,13 @@ void fused_io(const LevelIO& io, bool inverse, LevelArgs& a) {
 
 // A plan's own device memory (status word, one LL buffer per level), made on
 // its first single-image call: plans used only in batches never allocate.
+// The status allocation holds two words: the status, and a flag that
+// nothing sets (the injected hold of dwt_debug_inject waits on it).
 dwt_status ensure_device(dwt_plan_s* p) {
   cudaError_t e = cudaSuccess;
   if (!p->d_status) {
-    e = cudaMalloc(&p->d_status, sizeof(int));
-    if (e == cudaSuccess) e = cudaMemset(p->d_status, 0, sizeof(int));
+    e = dev_malloc(reinterpret_cast<void**>(&p->d_status), 2 * sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(p->d_status, 0, 2 * sizeof(int));
     if (e != cudaSuccess) {
       cudaFree(p->d_status);
       p->d_status = nullptr;
@@ -773,7 +850,7 @@ dwt_status ensure_device(dwt_plan_s* p) {
     for (int k = 0; k + 1 < p->levels; ++k) {
       const size_t pitch = round_up((size_t)p->W[k + 1] * p->es, 128);
       void* q = nullptr;
-      e = cudaMalloc(&q, pitch * p->H[k + 1]);
+      e = dev_malloc(&q, pitch * p->H[k + 1]);
       if (e != cudaSuccess) {
         for (void* r : p->ll) cudaFree(r);
         p->ll.clear();
@@ -1051,6 +1128,14 @@ dwt_status batch_submit(const dwt_request* reqs, int n, cudaStream_t s, int* d_s
     }
   }
   const int nl = (int)levels.size();
+  // injected failure: the second level of the first request waits for one
+  // more strip per row than its rows have, a count nothing reaches
+  if (injected(DWT_INJECT_BATCH_DEP))
+    for (BatchLevel& bl : levels)
+      if (bl.request == 0 && bl.dep_row_base >= 0) {
+        ++bl.dep_ncs;
+        break;
+      }
 
   std::vector<int2> row_deps(nrows, make_int2(0, -1));
   for (int l = 0; l < nl; ++l) {
@@ -1132,7 +1217,7 @@ dwt_status batch_submit(const dwt_request* reqs, int n, cudaStream_t s, int* d_s
     if (st.host) cudaFreeHost(st.host);
     st.host = nullptr;
     st.cap = 0;
-    e = cudaMallocHost(&st.host, upload * 2);
+    e = host_malloc(&st.host, upload * 2);
     if (e == cudaSuccess) st.cap = upload * 2;
   }
   if (e != cudaSuccess) return from_cuda(e);
@@ -1151,7 +1236,7 @@ dwt_status batch_submit(const dwt_request* reqs, int n, cudaStream_t s, int* d_s
   if (e != cudaSuccess) return from_cuda(e);
   // tensor maps read from global memory must be 64-byte aligned
   unsigned char* block = nullptr;
-  e = cudaMallocFromPoolAsync(reinterpret_cast<void**>(&block), off_head + counters + 128, pool, s);
+  e = pool_malloc(reinterpret_cast<void**>(&block), off_head + counters + 128, pool, s);
   if (e != cudaSuccess) return from_cuda(e);
   unsigned char* d = block + ((128 - (reinterpret_cast<uintptr_t>(block) & 127)) & 127);
   int* head = reinterpret_cast<int*>(d + off_head);
@@ -1173,6 +1258,9 @@ dwt_status batch_submit(const dwt_request* reqs, int n, cudaStream_t s, int* d_s
                                 reqs[i].out_pitch, ll.data(), ll_pitch[i].data());
     fused_io(io, inverse, a);
     a.status = status + i;
+    a.probes = g_ring_probes.load();
+    a.spins = g_dep_spins.load();
+    a.hold = nullptr;
     a.src_tma = encode_level_maps(&b.maps, p->dtype, a, kinfo[b.kind], p->es);
   }
   unsigned char* h = static_cast<unsigned char*>(st.host);
@@ -1219,9 +1307,13 @@ struct DeviceGuard {
 
 // ---------------------------------------------------------------------------
 // Forward transform on caller-provided scratch, for the entry point that
-// allocates nothing (noalloc.cu).  It mirrors the plan path's forward level
-// loop with the default scheme and tile, keeps its state on the stack, and
-// makes no device or host allocation.
+// allocates nothing (noalloc.cu).  It runs the plan path's forward level
+// loop with the default scheme (Monolithic* for float, the separable JPEG
+// 2000 order for int32) and the tile a fresh plan takes (the scheme's
+// default strip height and ring depth, the same deeper ring for levels
+// that fit one wave), keeps its state on the stack, and makes no device or
+// host allocation.  d_status points at two device words: the status word
+// and a flag that nothing sets (for the injected hold).
 // ---------------------------------------------------------------------------
 namespace dwt {
 
@@ -1251,7 +1343,11 @@ dwt_status forward_on_scratch(int w, int h, int wavelet, int levels, int dtype, 
   const size_t nsrc = plane_extent(w, h, src_pitch, es), ndst = plane_extent(w, h, dst_pitch, es);
   if (!device_pointer_ok(src, nsrc, device) || !device_pointer_ok(dst, ndst, device)) return DWT_EINVAL;
   if (overlaps(src, nsrc, dst, ndst)) return DWT_EINVAL;
-  // LL ping-pong: LL_0, LL_2, ... in the first region, LL_1, LL_3, ... in the second
+  // Two LL regions used in turn: LL_1, LL_3, ... in the first (ceil(h/2)
+  // rows), LL_2, LL_4, ... in the second (ceil(h/4) rows), rows at a
+  // 128-byte pitch of ceil(w/2) elements.  A level's kernel starts reading
+  // only after the previous level's grid completed, so overwriting LL_k
+  // with LL_{k+2} is safe.
   const size_t spitch = levels >= 2 ? round_up((size_t)Wk[1] * es, 128) : 0;
   const size_t need = levels >= 2 ? spitch * ((size_t)Hk[1] + Hk[2]) : 0;
   if (need > scratch_bytes) return DWT_EINVAL;
@@ -1261,6 +1357,7 @@ dwt_status forward_on_scratch(int w, int h, int wavelet, int levels, int dtype, 
   char* sbase = static_cast<char*>(scratch);
   void* sc[2] = {sbase, sbase + spitch * (size_t)Hk[1]};
   const Lifting L = lifting_of(wavelet);
+  const Tile tile{device, kDefaultStages, 0};
   for (int k = 0; k < levels; ++k) {
     LevelArgs a{};
     a.W = Wk[k];
@@ -1283,23 +1380,10 @@ dwt_status forward_on_scratch(int w, int h, int wavelet, int levels, int dtype, 
     std::memset(&ct, 0, sizeof ct);
     const LaunchKey key{wavelet, dtype, scheme, PASS_FUSED, 0, a.W >= 2 && a.H >= 2 ? 1 : 0};
     KernelInfo ki{};
-    if (!find_kernel(key, kDefaultStages, &ki)) return DWT_EUNSUPPORTED;
-    int sms = 0, per_sm = 0;
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
-    int optin = 0;
-    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
-    cudaFuncSetAttribute(ki.fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         optin > 0 ? optin : (int)ki.smem_bytes);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ki.fn, kWarpsPerCta * 32,
-                                                      ki.smem_bytes) != cudaSuccess)
-      per_sm = 1;
-    const int cap = std::max(sms, 1) * std::max(per_sm, 1);
-    a.ncs = (a.cw + ki.uq - 1) / ki.uq;
-    a.T = strip_height(kDefaultStripRows, a.ch, a.ncs, cap, ki.up + ki.down, chunk_rows(ki));
-    a.nrs = (a.ch + a.T - 1) / a.T;
-    a.wave_rows = wave_rows(a, cap);
-    a.nstages = (long long)a.ncs * a.nrs < cap ? kMaxStages : kDefaultStages;
+    const dwt_status g = level_geometry(tile, key, a, ki);
+    if (g != DWT_OK) return g;
     a.status = d_status;
+    set_waits(a, d_status + 1);
     TmaMaps maps;
     a.src_tma = encode_level_maps(&maps, dtype, a, ki, es);
     const LaunchCall call{&a, &maps, &cf, &ct, s};
@@ -1434,11 +1518,19 @@ static dwt_status host_call(dwt_plan p, bool inverse, const void* h_in, size_t i
   const size_t row = (size_t)p->w * p->es;
   if (in_pitch < row || out_pitch < row) return DWT_EINVAL;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  if (!p->stage_in) {
-    p->stage_pitch = round_up(row, 128);
-    cudaError_t e = cudaMalloc(&p->stage_in, p->stage_pitch * p->h);
-    if (e == cudaSuccess) e = cudaMalloc(&p->stage_out, p->stage_pitch * p->h);
-    if (e != cudaSuccess) return from_cuda(e);
+  if (!p->stage_in || !p->stage_out) {
+    // both staging planes or neither: a failure frees what was made
+    const size_t pitch = round_up(row, 128);
+    void *in = nullptr, *out = nullptr;
+    cudaError_t e = dev_malloc(&in, pitch * p->h);
+    if (e == cudaSuccess) e = dev_malloc(&out, pitch * p->h);
+    if (e != cudaSuccess) {
+      if (in) cudaFree(in);
+      return from_cuda(e);
+    }
+    p->stage_pitch = pitch;
+    p->stage_in = in;
+    p->stage_out = out;
   }
   cudaError_t e = cudaMemcpy2DAsync(p->stage_in, p->stage_pitch, h_in, in_pitch, row, p->h,
                                     cudaMemcpyHostToDevice, s);
@@ -1475,6 +1567,24 @@ dwt_status dwt_batch_submit(const dwt_request* reqs, int n, dwt_stream stream, i
   locks.reserve(plans.size());
   for (dwt_plan_s* p : plans) locks.emplace_back(p->mu);
   return batch_submit(reqs, n, reinterpret_cast<cudaStream_t>(stream), d_status);
+}
+
+dwt_status dwt_set_wait_limits(unsigned int ring_probes, unsigned int dep_spins) {
+  g_ring_probes.store(ring_probes ? ring_probes : kDefaultRingProbes);
+  g_dep_spins.store(dep_spins ? dep_spins : kDefaultDepSpins);
+  return DWT_OK;
+}
+
+dwt_status dwt_debug_inject(dwt_injection what, int skip, int count) {
+  if ((int)what < DWT_INJECT_NONE || (int)what > DWT_INJECT_BATCH_DEP || skip < 0 || count < 0)
+    return DWT_EINVAL;
+  std::lock_guard<std::mutex> lk(g_inject_mu);
+  if (what == DWT_INJECT_NONE) {
+    for (Injection& j : g_inject) j = Injection{};
+  } else {
+    g_inject[what] = Injection{skip, count};
+  }
+  return DWT_OK;
 }
 
 dwt_status dwt_plan_device_status(dwt_plan p) {
@@ -1531,8 +1641,8 @@ dwt_status dwt_plan_autotune(dwt_plan p, dwt_stream stream) {
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   const size_t pitch = round_up((size_t)p->w * p->es, 128);
   void *in = nullptr, *out = nullptr;
-  cudaError_t e = cudaMalloc(&in, pitch * p->h);
-  if (e == cudaSuccess) e = cudaMalloc(&out, pitch * p->h);
+  cudaError_t e = dev_malloc(&in, pitch * p->h);
+  if (e == cudaSuccess) e = dev_malloc(&out, pitch * p->h);
   if (e == cudaSuccess) e = cudaMemsetAsync(in, 0x3c, pitch * p->h, s);
   cudaEvent_t a = nullptr, b = nullptr;
   if (e == cudaSuccess) e = cudaEventCreate(&a);

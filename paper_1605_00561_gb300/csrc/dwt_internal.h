@@ -40,6 +40,13 @@ constexpr double kGamma = 0.882911075530934;
 constexpr double kDelta = 0.443506852043971;
 constexpr double kK97 = 1.230174104914001;
 
+// Default limits of the kernels' bounded waits: probes of a ring stage's
+// mbarrier (each probe may suspend the thread briefly) and polls of a row
+// counter or flag (each followed by a short nanosleep).  Both run to
+// seconds at most; dwt_set_wait_limits changes them for later launches.
+constexpr uint32_t kDefaultRingProbes = 1u << 24;
+constexpr uint32_t kDefaultDepSpins = 1u << 22;
+
 constexpr int kWarpsPerCta = 1;  // independent warps (one strip each) per CTA
 constexpr int kMaxStages = 4;    // ring depth per warp
 constexpr int kDefaultStages = 2;
@@ -81,6 +88,12 @@ struct LevelArgs {
   long long dst_pitch[4];
   int src_tma;   // bit p: the tensor map of source plane p is valid (TMA loads it)
   int* status;   // device error word (bit 0: a bounded wait ran out)
+  uint32_t probes;  // limit of a ring-stage wait (mbarrier probes)
+  uint32_t spins;   // limit of a row-counter or flag wait (polls)
+  // Failure injection (tests of the error paths): when set, the launch's
+  // first strip waits, bounded by `spins`, for this word to become nonzero;
+  // nothing sets it, so the wait runs out and the status word is raised.
+  const int* hold;
 };
 
 struct TmaMaps {

@@ -39,7 +39,6 @@
 namespace dwt {
 namespace dev {
 
-constexpr uint32_t kWaitProbes = 1u << 24;
 
 template <typename ST>
 struct StoreT;
@@ -697,16 +696,14 @@ __device__ __forceinline__ void strip_coords(int s, int ncs, int nrs, int wave_r
 // `need`.  Lane i watches rows lo + i, lo + i + 32, ...; each lane acquires
 // the writes of the strips it watched, and the warp barrier at the end
 // passes them on to the lanes that read the data.  Returns false if the
-// wait ran out.
-constexpr uint32_t kDepSpins = 1u << 22;  // x ~0.1-1 us of nanosleep: seconds at most
-
+// wait ran out (after `limit` polls, each followed by a short nanosleep).
 __device__ __forceinline__ int load_acquire(const int* p) {
   int v;
   asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
   return v;
 }
 
-__device__ __forceinline__ bool wait_rows(const int* dep, int lo, int hi, int need) {
+__device__ __forceinline__ bool wait_rows(const int* dep, int lo, int hi, int need, uint32_t limit) {
   const int lane = threadIdx.x & 31;
   bool ok = true;
   for (int r0 = lo; r0 <= hi && ok; r0 += 32) {
@@ -715,7 +712,7 @@ __device__ __forceinline__ bool wait_rows(const int* dep, int lo, int hi, int ne
     for (uint32_t spins = 0;; ++spins) {
       if (!mine) mine = load_acquire(dep + r) >= need;
       if (__all_sync(kFull, mine)) break;
-      if (spins >= kDepSpins) {
+      if (spins >= limit) {
         ok = false;
         break;
       }
@@ -727,6 +724,18 @@ __device__ __forceinline__ bool wait_rows(const int* dep, int lo, int hi, int ne
   // reads them by TMA (async proxy) as well
   ptx::fence_proxy_async_global();
   return ok;
+}
+
+// Failure injection: waits, bounded by `limit` polls, until *flag is
+// nonzero.  The flag passed is one that nothing sets, so the wait runs out;
+// it is taken before the strip issues any load, so no copy is in flight
+// when the warp leaves.
+__device__ __forceinline__ bool wait_flag(const int* flag, uint32_t limit) {
+  for (uint32_t spins = 0; spins < limit; ++spins) {
+    if (__any_sync(kFull, load_acquire(flag) != 0)) return true;
+    __nanosleep(64);
+  }
+  return false;
 }
 
 // Publishes a finished strip of row rs: after the warp barrier (which
@@ -781,14 +790,15 @@ __device__ __forceinline__ bool run_strip(const LevelArgs& a, const TmaMaps& map
     }
     const uint32_t g = g0 + c;
     const int s = g % NS;
-    bool ok = ptx::mbar_wait_bounded(&bars[s], (g / NS) & 1, kWaitProbes);
+    bool ok = ptx::mbar_wait_bounded(&bars[s], (g / NS) & 1, a.probes);
     ok = __all_sync(kFull, ok);
     if (!ok) {
       if (lane == 0) atomicOr(a.status, 1);
-      // let copies already in flight land before the warp leaves
+      // let copies already in flight land before the warp leaves (with the
+      // default limit, whatever limit the launch set for the wait above)
       ptx::cp_async_wait_all();
       for (int k = c; k < nchunks && k < c + NS; ++k)
-        ptx::mbar_wait_bounded(&bars[(g0 + k) % NS], ((g0 + k) / NS) & 1, kWaitProbes);
+        ptx::mbar_wait_bounded(&bars[(g0 + k) % NS], ((g0 + k) / NS) & 1, kDefaultRingProbes);
       chunk_ctr = g0 + nchunks;
       return false;
     }
@@ -829,6 +839,10 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, C::MIN_WARPS / kWarpsPerCta
       if ((a.src_tma >> p) & 1) ptx::prefetch_tensormap(&maps.m[p]);
   }
   __syncwarp();
+  if (a.hold && strip == 0 && !wait_flag(a.hold, a.spins)) {
+    if (lane == 0) atomicOr(a.status, 1);
+    return;
+  }
   int cs, rs;
   strip_coords(strip, a.ncs, a.nrs, a.wave_rows, cs, rs);
   // the previous level's kernel may still be running: every read and write

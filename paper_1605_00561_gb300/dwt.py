@@ -19,7 +19,8 @@ __all__ = [
     "SCHEMES", "DWT_NORM_JPEG2000", "DWT_NORM_ZETA",
     "dwt_plan_create", "dwt_plan_set_scheme", "dwt_plan_set_tile", "dwt_plan_get_tile", "dwt_plan_get_scheme", "dwt_plan_set_normalization",
     "dwt2_forward", "dwt2_inverse", "dwt2_forward_noalloc", "dwt2_forward_host", "dwt2_inverse_host", "dwt_batch_submit",
-    "dwt_plan_device_status", "dwt_plan_set_profiling", "dwt_plan_read_profile", "dwt_plan_autotune",
+    "dwt_plan_device_status", "dwt_noalloc_device_status", "dwt_set_wait_limits", "dwt_debug_inject",
+    "DWT_INJECT_NONE", "DWT_INJECT_ENOMEM", "DWT_INJECT_HOLD", "DWT_INJECT_BATCH_DEP", "dwt_plan_set_profiling", "dwt_plan_read_profile", "dwt_plan_autotune",
     "dwt_plan_destroy", "dwt_status_string", "dwt_version", "Plan", "DwtRequest",
 ]
 
@@ -29,6 +30,7 @@ DWT_OK, DWT_EINVAL, DWT_ENOMEM, DWT_EUNSUPPORTED, DWT_ECUDA, DWT_ETIMEOUT, DWT_E
 DWT_CDF53, DWT_CDF97, DWT_DD137 = 0, 1, 2
 DWT_F32, DWT_F16S, DWT_I32 = 0, 1, 2
 DWT_NORM_JPEG2000, DWT_NORM_ZETA = 0, 1
+DWT_INJECT_NONE, DWT_INJECT_ENOMEM, DWT_INJECT_HOLD, DWT_INJECT_BATCH_DEP = range(4)
 SCHEMES = {
     "auto": 0, "rowcol": 1, "sweldens": 2, "iwahashi": 3, "iwahashi*": 4, "explosive": 5,
     "explosive*": 6, "monolithic": 7, "monolithic*": 8, "polyphase": 9, "polyphase*": 10,
@@ -77,6 +79,9 @@ EXPORTS = {
     "dwt_batch_submit": ([ctypes.POINTER(DwtRequest), ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p],
                          ctypes.c_int),
     "dwt_plan_device_status": ([ctypes.c_void_p], ctypes.c_int),
+    "dwt_noalloc_device_status": ([ctypes.c_void_p], ctypes.c_int),
+    "dwt_set_wait_limits": ([ctypes.c_uint, ctypes.c_uint], ctypes.c_int),
+    "dwt_debug_inject": ([ctypes.c_int, ctypes.c_int, ctypes.c_int], ctypes.c_int),
     "dwt_plan_set_profiling": ([ctypes.c_void_p, ctypes.c_int], ctypes.c_int),
     "dwt_plan_read_profile": ([ctypes.c_void_p, ctypes.POINTER(KernelStat), ctypes.c_int,
                                ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
@@ -159,7 +164,8 @@ def dwt2_inverse(plan: int, d_coef: int, coef_pitch: int, d_out: int, out_pitch:
 def dwt2_forward_noalloc(w: int, h: int, wavelet: int, levels: int, dtype: int, d_in: int, in_pitch: int,
                          d_out: int, out_pitch: int, stream: int = 0) -> None:
     """Forward transform without a plan and without any device allocation
-    (scratch in a fixed 32 MiB device array of the library; see dwt.h)."""
+    (scratch in a fixed 32 MiB device array of the library; see dwt.h).
+    Device-side timeouts are read with :func:`dwt_noalloc_device_status`."""
     _check(lib().dwt2_forward_noalloc(w, h, wavelet, levels, dtype, d_in, in_pitch, d_out, out_pitch, stream),
            "dwt2_forward_noalloc")
 
@@ -180,6 +186,18 @@ def dwt_batch_submit(reqs: Sequence[DwtRequest], stream: int = 0, d_status: int 
 
 def dwt_plan_device_status(plan: int) -> int:
     return lib().dwt_plan_device_status(plan)
+
+
+def dwt_noalloc_device_status(stream: int = 0) -> int:
+    return lib().dwt_noalloc_device_status(stream)
+
+
+def dwt_set_wait_limits(ring_probes: int = 0, dep_spins: int = 0) -> None:
+    _check(lib().dwt_set_wait_limits(ring_probes, dep_spins), "dwt_set_wait_limits")
+
+
+def dwt_debug_inject(what: int, skip: int = 0, count: int = 0) -> None:
+    _check(lib().dwt_debug_inject(what, skip, count), "dwt_debug_inject")
 
 
 def dwt_plan_set_profiling(plan: int, enable: bool) -> None:

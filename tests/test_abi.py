@@ -73,3 +73,14 @@ def test_binding_raises_on_missing_library(monkeypatch, tmp_path):
     monkeypatch.setattr(dwt, "LIB_PATH", str(tmp_path / "nope.so"))
     with pytest.raises(ImportError):
         dwt.lib()
+
+
+def test_wait_limits_and_injection_arguments(libdwt):
+    lib = libdwt.lib()
+    assert lib.dwt_set_wait_limits(0, 0) == libdwt.DWT_OK
+    assert lib.dwt_debug_inject(libdwt.DWT_INJECT_NONE, 0, 0) == libdwt.DWT_OK
+    assert lib.dwt_debug_inject(4, 0, 1) == libdwt.DWT_EINVAL
+    assert lib.dwt_debug_inject(-1, 0, 1) == libdwt.DWT_EINVAL
+    assert lib.dwt_debug_inject(libdwt.DWT_INJECT_ENOMEM, -1, 1) == libdwt.DWT_EINVAL
+    assert lib.dwt_debug_inject(libdwt.DWT_INJECT_ENOMEM, 0, -1) == libdwt.DWT_EINVAL
+    assert lib.dwt_debug_inject(libdwt.DWT_INJECT_NONE, 0, 0) == libdwt.DWT_OK

@@ -1,0 +1,153 @@
+"""Parity at the stated workload configurations that the shape sweep of
+test_gpu_parity.py does not reach:
+
+* the 512 x 512 float32 image of uniform integers 0..255 (seed 1), one level
+  of float CDF 5/3 forward then inverse, with the reduced-barrier schemes;
+* float CDF 5/3 at 8192 x 8192 (textured input), 1 and 6 levels, where the
+  strips are dealt over several resident waves;
+* six levels of every float scheme at 2048 x 2048, both CDF wavelets, and
+  DD 13/7 for the schemes that take it;
+* a mixed batch drawn like the 256-image workload (sides uniform in
+  [256, 4096], 3 levels, half CDF 9/7 float32, half reversible 5/3 int32),
+  32 images.
+
+Every coefficient is compared with the FP64 / exact-integer oracle: float32
+within 2e-3 (the stated bar), a GPU forward followed by a GPU inverse within
+twice that, integers bit-exact."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1605_00561_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+TOL_F32 = 2e-3
+TOL_ROUND_TRIP = 2 * TOL_F32
+OID = {"cdf53": oracle.CDF53, "cdf97": oracle.CDF97, "dd137": oracle.DD137}
+FLOAT_SCHEMES = ["rowcol", "sweldens", "iwahashi", "iwahashi*", "explosive", "explosive*",
+                 "monolithic", "monolithic*", "polyphase", "polyphase*", "convolution"]
+DD_SCHEMES = ["rowcol", "sweldens", "iwahashi", "iwahashi*", "explosive", "explosive*", "monolithic",
+              "monolithic*"]
+
+
+@pytest.fixture(scope="module")
+def dwt():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1605_00561_gb300 import dwt as d
+    d.lib()
+    return d
+
+
+def check_fwd_inv(dwt, x, ref, wavelet, levels, scheme):
+    """Forward against the oracle, inverse of the oracle's coefficients
+    against the input, and the GPU round trip."""
+    h, w = x.shape
+    plan = dwt.Plan(w, h, wavelet, levels, "f32", scheme=scheme)
+    xd = torch.from_numpy(np.ascontiguousarray(x)).cuda()
+    c = torch.empty_like(xd)
+    y = torch.empty_like(xd)
+    yo = torch.empty_like(xd)
+    plan.forward(xd, c)
+    plan.inverse(c, y)
+    plan.inverse(torch.from_numpy(ref.astype(np.float32)).cuda(), yo)
+    torch.cuda.synchronize()
+    assert dwt.dwt_plan_device_status(plan.handle) == dwt.DWT_OK
+    plan.close()
+    ef = float((c.double() - torch.from_numpy(ref).cuda()).abs().max())
+    ei = float((yo - xd).abs().max())
+    er = float((y - xd).abs().max())
+    assert ef <= TOL_F32, ("forward", scheme, ef)
+    assert ei <= TOL_F32, ("inverse of oracle coefficients", scheme, ei)
+    assert er <= TOL_ROUND_TRIP, ("round trip", scheme, er)
+
+
+@pytest.mark.parametrize("scheme", ["monolithic", "monolithic*", "sweldens", "polyphase*", "iwahashi*",
+                                    "explosive*"])
+def test_512_uniform_cdf53_one_level(dwt, scheme):
+    x = inputs.uniform_image(512, 512, seed=1)
+    ref = oracle.dwt2(x.astype(np.float64), oracle.CDF53, 1)
+    check_fwd_inv(dwt, x, ref, "cdf53", 1, scheme)
+
+
+_ref_8192 = {}
+
+
+def _oracle_8192(levels):
+    if levels not in _ref_8192:
+        x = inputs.textured_image(8192, 8192, seed=4)
+        _ref_8192.clear()
+        _ref_8192[levels] = (x, oracle.dwt2(x.astype(np.float64), oracle.CDF53, levels))
+    return _ref_8192[levels]
+
+
+@pytest.mark.parametrize("levels", [1, 6])
+@pytest.mark.parametrize("scheme", ["monolithic*", "sweldens", "polyphase", "convolution"])
+def test_cdf53_8192_full_compare(dwt, levels, scheme):
+    x, ref = _oracle_8192(levels)
+    check_fwd_inv(dwt, x, ref, "cdf53", levels, scheme)
+
+
+_ref_2048 = {}
+
+
+def _oracle_2048(wavelet):
+    if wavelet not in _ref_2048:
+        x = inputs.textured_image(2048, 2048, seed=5)
+        _ref_2048[wavelet] = (x, oracle.dwt2(x.astype(np.float64), OID[wavelet], 6))
+    return _ref_2048[wavelet]
+
+
+@pytest.mark.parametrize("scheme", FLOAT_SCHEMES)
+@pytest.mark.parametrize("wavelet", ["cdf53", "cdf97"])
+def test_six_levels_2048_every_scheme(dwt, wavelet, scheme):
+    x, ref = _oracle_2048(wavelet)
+    check_fwd_inv(dwt, x, ref, wavelet, 6, scheme)
+
+
+@pytest.mark.parametrize("scheme", DD_SCHEMES)
+def test_six_levels_2048_dd137(dwt, scheme):
+    x, ref = _oracle_2048("dd137")
+    check_fwd_inv(dwt, x, ref, "dd137", 6, scheme)
+
+
+def test_mixed_batch_like_the_256_image_workload(dwt):
+    """32 images of the 256-image recipe (its seed, sides uniform in [256,
+    4096], odd sizes included), 3 levels, first half CDF 9/7 float32 on
+    8-bit inputs, second half reversible 5/3 int32 on 12-bit inputs, in one
+    batch; then the inverse batch of the coefficients."""
+    L = 3
+    shapes = inputs.batch_shapes(32, seed=8)
+    plans, xs, cs, ys, refs = [], [], [], [], []
+    for i, (w, h, kind) in enumerate(shapes):
+        if kind == "cdf97":
+            x = inputs.uniform_image(h, w, seed=100 + i)
+            plans.append(dwt.Plan(w, h, "cdf97", L, "f32"))
+            refs.append(oracle.dwt2(x.astype(np.float64), oracle.CDF97, L))
+        else:
+            x = inputs.int12_image(h, w, seed=100 + i)
+            plans.append(dwt.Plan(w, h, "cdf53", L, "i32"))
+            refs.append(oracle.dwt2_int(x, L))
+        xs.append(torch.from_numpy(x).cuda())
+        cs.append(torch.empty_like(xs[-1]))
+        ys.append(torch.empty_like(xs[-1]))
+    status = torch.full((len(shapes),), 9, dtype=torch.int32, device="cuda")
+    dwt.submit([p.request(x, c) for p, x, c in zip(plans, xs, cs)], status=status)
+    torch.cuda.synchronize()
+    assert status.cpu().tolist() == [dwt.DWT_OK] * len(shapes)
+    dwt.submit([p.request(c, y, inverse=True) for p, c, y in zip(plans, cs, ys)], status=status)
+    torch.cuda.synchronize()
+    assert status.cpu().tolist() == [dwt.DWT_OK] * len(shapes)
+    for (w, h, kind), x, c, y, ref in zip(shapes, xs, cs, ys, refs):
+        got = c.cpu().numpy()
+        if kind == "cdf97":
+            assert np.abs(got - ref).max() <= TOL_F32, (w, h)
+            assert float((y - x).abs().max()) <= TOL_ROUND_TRIP, (w, h)
+        else:
+            assert np.array_equal(got, ref), (w, h)
+            assert torch.equal(y, x), (w, h)
+    for p in plans:
+        p.close()

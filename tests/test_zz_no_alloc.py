@@ -1,9 +1,12 @@
-"""dwt2_forward_noalloc, the forward transform for callers that cannot
-allocate device memory (graph capture, real-time loops, hosts that own all
-allocations): its LL scratch is a fixed device array inside the library.
-Checked through the C ABI against dwt2_forward with a plan, twice in a row
-(the shared array keeps the previous call's contents).  This file is
-collected last on purpose."""
+"""dwt2_forward_noalloc: the forward transform for callers that cannot
+allocate device memory -- a real-time loop that must not call cudaMalloc
+(which can synchronise the device and take unbounded time), or a plug-in
+whose host application owns every device allocation.  Its LL scratch is a
+fixed device array inside the library.  Checked through the C ABI against
+dwt2_forward with a plan, twice in a row (the shared array keeps the
+previous call's contents); the call's device memory use is checked too,
+and a device wait that runs out is read back through
+dwt_noalloc_device_status.  This file is collected last on purpose."""
 import numpy as np
 import pytest
 
@@ -22,7 +25,9 @@ def dwt():
         pytest.skip("no CUDA device")
     from paper_1605_00561_gb300 import dwt as d
     d.lib()
-    return d
+    yield d
+    d.dwt_debug_inject(d.DWT_INJECT_NONE)
+    d.dwt_set_wait_limits(0, 0)
 
 
 def _plan_forward(dwt, x, wavelet, levels, dtype):
@@ -33,6 +38,12 @@ def _plan_forward(dwt, x, wavelet, levels, dtype):
     torch.cuda.synchronize()
     plan.close()
     return out
+
+
+def _noalloc(dwt, x, out, wl, levels, dt, stream=0):
+    h, w = x.shape
+    dwt.dwt2_forward_noalloc(w, h, wl, levels, dt, x.data_ptr(), x.stride(0) * x.element_size(),
+                             out.data_ptr(), out.stride(0) * out.element_size(), stream)
 
 
 @pytest.mark.parametrize("wavelet,dtype,h,w,levels", [
@@ -50,15 +61,46 @@ def test_noalloc_matches_plan_forward_twice(dwt, wavelet, dtype, h, w, levels):
             x = torch.from_numpy(inputs.uniform_image(h, w, seed=seed)).cuda()
         ref = _plan_forward(dwt, x, wavelet, levels, dtype).cpu().numpy()
         out = torch.full_like(x, -7)
-        dwt.dwt2_forward_noalloc(w, h, wl, levels, dt, x.data_ptr(), x.stride(0) * x.element_size(),
-                                 out.data_ptr(), out.stride(0) * out.element_size(),
-                                 torch.cuda.current_stream().cuda_stream)
+        _noalloc(dwt, x, out, wl, levels, dt, torch.cuda.current_stream().cuda_stream)
         torch.cuda.synchronize()
         got = out.cpu().numpy()
         if dtype == "i32":
             assert np.array_equal(got, ref), f"call {call}"
         else:
             assert np.abs(got.astype(np.float64) - ref).max() <= TOL_F32, f"call {call}"
+    assert dwt.dwt_noalloc_device_status(0) == dwt.DWT_OK
+
+
+def test_noalloc_call_takes_no_device_memory(dwt):
+    """After a first call (which looks up the array and loads the kernels),
+    a call leaves the device's free memory and torch's allocation as they
+    were."""
+    h, w, L = 1024, 768, 5
+    x = torch.from_numpy(inputs.uniform_image(h, w, seed=5)).cuda()
+    out = torch.empty_like(x)
+    _noalloc(dwt, x, out, dwt.DWT_CDF97, L, dwt.DWT_F32)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    alloc0 = torch.cuda.memory_allocated()
+    _noalloc(dwt, x, out, dwt.DWT_CDF97, L, dwt.DWT_F32)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0 and torch.cuda.memory_allocated() == alloc0
+
+
+def test_noalloc_wait_timeout_is_reported_then_clean(dwt):
+    h, w, L = 300, 521, 4
+    x = torch.from_numpy(inputs.uniform_image(h, w, seed=41)).cuda()
+    ref = _plan_forward(dwt, x, "cdf97", L, "f32").cpu().numpy()
+    out = torch.empty_like(x)
+    dwt.dwt_set_wait_limits(0, 2000)
+    dwt.dwt_debug_inject(dwt.DWT_INJECT_HOLD, 0, 1)  # the first level's launch waits on a flag nothing sets
+    _noalloc(dwt, x, out, dwt.DWT_CDF97, L, dwt.DWT_F32)
+    assert dwt.dwt_noalloc_device_status(0) == dwt.DWT_ETIMEOUT
+    dwt.dwt_set_wait_limits(0, 0)
+    _noalloc(dwt, x, out, dwt.DWT_CDF97, L, dwt.DWT_F32)
+    assert dwt.dwt_noalloc_device_status(0) == dwt.DWT_OK
+    assert np.abs(out.cpu().numpy().astype(np.float64) - ref).max() <= TOL_F32
 
 
 def test_noalloc_rejects_images_beyond_its_scratch(dwt):
