@@ -124,6 +124,19 @@ dwt_status dwt_plan_set_scheme(dwt_plan plan, dwt_scheme scheme);
  * of range. */
 dwt_status dwt_plan_set_tile(dwt_plan plan, int strip_rows, int stages);
 
+/* Fused tail of the pyramid (the paper's multi-level transform, Sec. 1,
+ * run as in-tile levels, Sec. 6): levels whose input has at most
+ * `max_pixels` samples, and both sides >= 2, run together in one launch in
+ * which each level is cut into 2-D tiles held in shared memory (one
+ * barrier per step that reads other quadruples) and the levels are
+ * separated by a grid-wide barrier.  The larger levels keep one streaming
+ * launch each.  -1 restores the default (2048 x 2048 samples), 0 turns the
+ * fusion off.  Row-column and Convolution plans never fuse.  The result is
+ * the same transform (float: within rounding of the per-level kernels;
+ * int32: bit-identical).  Errors: DWT_EINVAL for values below -1. */
+dwt_status dwt_plan_set_fusion(dwt_plan plan, long long max_pixels);
+dwt_status dwt_plan_get_fusion(dwt_plan plan, long long* max_pixels);
+
 /* The tile the plan's calls use: set by dwt_plan_set_tile, else the
  * autotuner's choice for this plan (from dwt_plan_autotune or the cache
  * file), else the defaults.  Either pointer may be NULL. */

@@ -6,6 +6,7 @@
 #include <type_traits>
 
 #include "level_kernel.cuh"
+#include "tile_kernel.cuh"
 
 namespace dwt {
 
@@ -87,6 +88,57 @@ inline bool fused_float(const LaunchKey& k, int ns, KernelInfo* info, const Laun
   }
   if (k.wavelet == W53 && k.dtype == F16S) return fused_dir<SCHEME, W53, __half, false>(inv, ns, info, call, err);
   if (k.wavelet == W97 && k.dtype == F16S) return fused_dir<SCHEME, W97, __half, false>(inv, ns, info, call, err);
+  return false;
+}
+
+// ---- fused-tail kernels (tile_kernel.cuh) ----------------------------------
+template <class C>
+inline bool run_tail(TailInfo* info, const TailCall* call, cudaError_t* err) {
+  using I = TailInstance<C>;
+  if (info) {
+    I::geom(&info->inner_rows, &info->inner_cols);
+    info->smem_bytes = I::smem();
+    info->fn = I::fn();
+  }
+  if (call) *err = I::launch(*call->p, call->blocks, call->stream);
+  return true;
+}
+
+template <int SCHEME, int WL, typename ST, bool INV, bool STATIC>
+using TailFusedCfg = TailCfg<ST, float, typename FusedProgram<SCHEME, WL, INV>::type, INV ? SUBBANDS : SAMPLES,
+                             INV ? SAMPLES : SUBBANDS, std::conditional_t<STATIC, StCoefs<WL, INV>, RtTag>>;
+
+template <int SCHEME, int WL, typename ST, bool STATIC>
+inline bool tail_dir(bool inv, TailInfo* info, const TailCall* call, cudaError_t* err) {
+  return inv ? run_tail<TailFusedCfg<SCHEME, WL, ST, true, STATIC>>(info, call, err)
+             : run_tail<TailFusedCfg<SCHEME, WL, ST, false, STATIC>>(info, call, err);
+}
+
+// The float tail kernels of one scheme: CDF 5/3 and 9/7 in float32 and
+// float16 storage, DD 13/7 in float32 where the scheme takes it; static
+// coefficients for JPEG 2000 normalisation (a tail level has both sides >= 2).
+template <int SCHEME>
+inline bool tail_float(const LaunchKey& k, TailInfo* info, const TailCall* call, cudaError_t* err) {
+  if (k.pass != PASS_FUSED || k.scheme != SCHEME) return false;
+  const bool inv = k.inverse != 0;
+  const bool st = k.static_coefs != 0;
+  if (k.wavelet == W53 && k.dtype == F32)
+    return st ? tail_dir<SCHEME, W53, float, true>(inv, info, call, err)
+              : tail_dir<SCHEME, W53, float, false>(inv, info, call, err);
+  if (k.wavelet == W97 && k.dtype == F32)
+    return st ? tail_dir<SCHEME, W97, float, true>(inv, info, call, err)
+              : tail_dir<SCHEME, W97, float, false>(inv, info, call, err);
+  if (k.wavelet == W53 && k.dtype == F16S)
+    return st ? tail_dir<SCHEME, W53, __half, true>(inv, info, call, err)
+              : tail_dir<SCHEME, W53, __half, false>(inv, info, call, err);
+  if (k.wavelet == W97 && k.dtype == F16S)
+    return st ? tail_dir<SCHEME, W97, __half, true>(inv, info, call, err)
+              : tail_dir<SCHEME, W97, __half, false>(inv, info, call, err);
+  if constexpr (kHasDegree3<SCHEME>) {
+    if (k.wavelet == WDD && k.dtype == F32)
+      return st ? tail_dir<SCHEME, WDD, float, true>(inv, info, call, err)
+                : tail_dir<SCHEME, WDD, float, false>(inv, info, call, err);
+  }
   return false;
 }
 

@@ -218,6 +218,25 @@ cudaError_t call_kernel(const LaunchKey& k, int ns, const LaunchCall& call) {
   return cudaErrorInvalidDeviceFunction;
 }
 
+const TailFn kTails[] = {tail_sweldens,   tail_iwahashi,    tail_iwahashi_s, tail_explosive, tail_explosive_s,
+                         tail_monolithic, tail_monolithic_s, tail_polyphase, tail_polyphase_s};
+
+bool find_tail(const LaunchKey& k, TailInfo* info) {
+  for (TailFn g : kTails) {
+    cudaError_t e = cudaSuccess;
+    if (g(k, info, nullptr, &e)) return true;
+  }
+  return false;
+}
+
+cudaError_t call_tail(const LaunchKey& k, const TailCall& call) {
+  for (TailFn g : kTails) {
+    cudaError_t e = cudaSuccess;
+    if (g(k, nullptr, &call, &e)) return e;
+  }
+  return cudaErrorInvalidDeviceFunction;
+}
+
 struct Occ {
   int sms = 0;
   int per_sm = 0;
@@ -236,9 +255,10 @@ constexpr int kOccSlots = 1024;
 std::mutex g_occ_mu;
 OccEntry g_occ[kOccSlots];
 
-// Resident blocks of one warp for kernel `fn` with `smem` bytes of dynamic
-// shared memory per block.
-Occ occupancy(const void* fn, size_t smem, int device) {
+// Resident blocks of `threads` threads (one warp by default) for kernel
+// `fn` with `smem` bytes of dynamic shared memory per block.  A kernel is
+// always queried with the same block size, so `fn` identifies it.
+Occ occupancy(const void* fn, size_t smem, int device, int threads = kWarpsPerCta * 32) {
   std::lock_guard<std::mutex> lk(g_occ_mu);
   const size_t hsh = (reinterpret_cast<uintptr_t>(fn) >> 4) * 31u + (size_t)device * 131u + smem;
   int free_slot = -1;
@@ -255,7 +275,7 @@ Occ occupancy(const void* fn, size_t smem, int device) {
   int optin = 0;
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
   cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, optin > 0 ? optin : (int)smem);
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o.per_sm, fn, kWarpsPerCta * 32, smem) != cudaSuccess)
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o.per_sm, fn, threads, smem) != cudaSuccess)
     o.per_sm = 1;
   o.sms = std::max(o.sms, 1);
   o.per_sm = std::max(o.per_sm, 1);
@@ -388,6 +408,10 @@ constexpr int kBatchStripRows = 48;
 // of a side stay far from int overflow.
 constexpr int kMaxSide = 1 << 28;
 
+// Levels whose input has at most this many samples run in the fused tail
+// (tile_kernel.cuh) by default: one launch for all of them.
+constexpr long long kDefaultFusePx = 2048LL * 2048LL;
+
 // Quad rows per strip.  Strips of about ten rows keep several waves of
 // one-warp blocks in flight, so the block scheduler balances SMs that
 // progress at different rates, while the vertical halo re-reads hit L2
@@ -500,6 +524,7 @@ struct dwt_plan_s {
   std::vector<cudaEvent_t> pool;
   int nstages = kDefaultStages;
   int strip_rows = 0;  // 0: the default of the scheme a call runs (default_strip_rows)
+  long long fuse_px = -1;  // fused-tail threshold (samples per level input); -1 default, 0 off
   bool tile_set = false;  // the caller chose the tile: the autotuner's choice does not apply
   bool tuned = false;     // the autotuner cache was consulted
   std::mutex mu;
@@ -833,13 +858,14 @@ void fused_io(const LevelIO& io, bool inverse, LevelArgs& a) {
 
 // A plan's own device memory (status word, one LL buffer per level), made on
 // its first single-image call: plans used only in batches never allocate.
-// The status allocation holds two words: the status, and a flag that
-// nothing sets (the injected hold of dwt_debug_inject waits on it).
+// The status allocation holds four words: the status, a flag that nothing
+// sets (the injected hold of dwt_debug_inject waits on it), the fused
+// tail's grid-barrier counter and a spare.
 dwt_status ensure_device(dwt_plan_s* p) {
   cudaError_t e = cudaSuccess;
   if (!p->d_status) {
-    e = dev_malloc(reinterpret_cast<void**>(&p->d_status), 2 * sizeof(int));
-    if (e == cudaSuccess) e = cudaMemset(p->d_status, 0, 2 * sizeof(int));
+    e = dev_malloc(reinterpret_cast<void**>(&p->d_status), 4 * sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(p->d_status, 0, 4 * sizeof(int));
     if (e != cudaSuccess) {
       cudaFree(p->d_status);
       p->d_status = nullptr;
@@ -883,7 +909,152 @@ dwt_status check_buffers(const dwt_plan_s* p, const void* src, size_t src_pitch,
   return DWT_OK;
 }
 
-// The transform proper: levels in order (forward) or reverse (inverse).
+// One level of a single-image call with the streaming kernels: the fused
+// scheme in one launch, or the row-column baseline's two passes.
+dwt_status run_level(dwt_plan_s* p, bool inverse, int k, int scheme, const Lifting& L, const void* src,
+                     size_t src_pitch, void* dst, size_t dst_pitch, void* const* ll, const size_t* llp,
+                     cudaStream_t s) {
+  const size_t es = p->es;
+  char slot[32];
+  LevelArgs a{};
+  level_dims(p, k, a);
+  const LevelIO io = level_io(p, inverse, k, a, src, src_pitch, dst, dst_pitch, ll, llp);
+  const void* const* band = io.band;
+  const long long* bpitch = io.bpitch;
+  const void* samples = io.samples;
+  const long long spitch = io.spitch;
+  const Coefs cf = make_coefs(L, p->norm, a.W, a.H, PASS_FUSED, inverse);
+  ConvTaps ct;
+  std::memset(&ct, 0, sizeof ct);
+  if (scheme == DWT_CONVOLUTION && !conv_taps(L, p->norm, a.W, a.H, inverse, &ct)) return DWT_EUNSUPPORTED;
+  if (scheme != DWT_ROWCOL) {
+    LaunchKey key{p->wavelet, p->dtype, scheme, PASS_FUSED, inverse ? 1 : 0,
+                  p->norm == DWT_NORM_JPEG2000 && a.W >= 2 && a.H >= 2 ? 1 : 0};
+    fused_io(io, inverse, a);
+    std::snprintf(slot, sizeof slot, "%s/L%d", inverse ? "inv" : "fwd", k);
+    return launch(p, key, a, cf, ct, s, slot);
+  }
+  // row-column: vertical pass and horizontal pass through p->tmp
+  const long long tp = (long long)(p->tmp_pitch / es);
+  LevelArgs v = a, hz = a;
+  const Coefs cv = make_coefs(L, p->norm, a.W, a.H, PASS_VERT, inverse);
+  const Coefs chz = make_coefs(L, p->norm, a.W, a.H, PASS_HORZ, inverse);
+  LaunchKey kv{p->wavelet, p->dtype, DWT_ROWCOL, PASS_VERT, inverse ? 1 : 0};
+  LaunchKey kh{p->wavelet, p->dtype, DWT_ROWCOL, PASS_HORZ, inverse ? 1 : 0};
+  dwt_status st;
+  if (!inverse) {
+    v.src[0] = samples;
+    v.src_pitch[0] = spitch;
+    v.dst[0] = p->tmp;
+    v.dst_pitch[0] = tp;
+    hz.src[0] = p->tmp;
+    hz.src_pitch[0] = tp;
+    for (int i = 0; i < 4; ++i) {
+      hz.dst[i] = const_cast<void*>(band[i]);
+      hz.dst_pitch[i] = bpitch[i];
+    }
+    std::snprintf(slot, sizeof slot, "fwd-v/L%d", k);
+    st = launch(p, kv, v, cv, ct, s, slot);
+    if (st != DWT_OK) return st;
+    std::snprintf(slot, sizeof slot, "fwd-h/L%d", k);
+    return launch(p, kh, hz, chz, ct, s, slot);
+  }
+  for (int i = 0; i < 4; ++i) {
+    hz.src[i] = band[i];
+    hz.src_pitch[i] = bpitch[i];
+  }
+  hz.dst[0] = p->tmp;
+  hz.dst_pitch[0] = tp;
+  v.src[0] = p->tmp;
+  v.src_pitch[0] = tp;
+  v.dst[0] = const_cast<void*>(samples);
+  v.dst_pitch[0] = spitch;
+  std::snprintf(slot, sizeof slot, "inv-h/L%d", k);
+  st = launch(p, kh, hz, chz, ct, s, slot);
+  if (st != DWT_OK) return st;
+  std::snprintf(slot, sizeof slot, "inv-v/L%d", k);
+  return launch(p, kv, v, cv, ct, s, slot);
+}
+
+// The levels [k0, k1) a call runs in the fused tail (k0 == k1: none): from
+// the first level whose input has at most the plan's threshold of samples,
+// while both sides stay >= 2, at most kMaxTailLevels, for every scheme with
+// a tile program (not row-column or Convolution).
+void tail_range(const dwt_plan_s* p, int scheme, bool inverse, int* k0, int* k1) {
+  *k0 = *k1 = p->levels;
+  const long long fp = p->fuse_px < 0 ? kDefaultFusePx : p->fuse_px;
+  if (fp == 0 || scheme == DWT_ROWCOL || scheme == DWT_CONVOLUTION) return;
+  int a = 0;
+  while (a < p->levels && (long long)p->W[a] * p->H[a] > fp) ++a;
+  int b = a;
+  while (b < p->levels && b - a < kMaxTailLevels && p->W[b] >= 2 && p->H[b] >= 2) ++b;
+  if (b == a) return;
+  TailInfo ti{};
+  const LaunchKey key{p->wavelet, p->dtype, scheme, PASS_FUSED, inverse ? 1 : 0,
+                      p->norm == DWT_NORM_JPEG2000 ? 1 : 0};
+  if (!find_tail(key, &ti)) return;
+  *k0 = a;
+  *k1 = b;
+}
+
+// Levels [k0, k1) of a call in one launch of the fused-tail kernel, in
+// processing order (finest first forward, coarsest first inverse).
+dwt_status run_tail(dwt_plan_s* p, bool inverse, int k0, int k1, int scheme, const Lifting& L, const void* src,
+                    size_t src_pitch, void* dst, size_t dst_pitch, void* const* ll, const size_t* llp,
+                    cudaStream_t s) {
+  const LaunchKey key{p->wavelet, p->dtype, scheme, PASS_FUSED, inverse ? 1 : 0,
+                      p->norm == DWT_NORM_JPEG2000 ? 1 : 0};
+  TailInfo ti{};
+  if (!find_tail(key, &ti)) return DWT_EUNSUPPORTED;
+  TailParams tp;
+  std::memset(&tp, 0, sizeof tp);
+  long long max_tiles = 0;
+  double bytes = 0.0;
+  for (int i = 0; i < k1 - k0; ++i) {
+    const int k = inverse ? k1 - 1 - i : k0 + i;
+    TileLevel& tl = tp.lv[i];
+    level_dims(p, k, tl.a);
+    const LevelIO io = level_io(p, inverse, k, tl.a, src, src_pitch, dst, dst_pitch, ll, llp);
+    fused_io(io, inverse, tl.a);
+    tl.a.status = p->d_status;
+    if (i == 0) {
+      set_waits(tl.a, p->d_status + 1);  // one injected hold per launch at most
+    } else {
+      tl.a.probes = tp.lv[0].a.probes;
+      tl.a.spins = tp.lv[0].a.spins;
+      tl.a.hold = nullptr;
+    }
+    tl.cf = make_coefs(L, p->norm, tl.a.W, tl.a.H, PASS_FUSED, inverse);
+    tl.ntx = (tl.a.cw + ti.inner_cols - 1) / ti.inner_cols;
+    tl.nty = (tl.a.ch + ti.inner_rows - 1) / ti.inner_rows;
+    max_tiles = std::max(max_tiles, (long long)tl.ntx * tl.nty);
+    bytes += 2.0 * tl.a.W * (double)tl.a.H * p->es;
+  }
+  tp.nlevels = k1 - k0;
+  tp.barrier = reinterpret_cast<unsigned*>(p->d_status + 2);
+  const Occ oc = occupancy(ti.fn, ti.smem_bytes, p->device, kTileThreads);
+  const int blocks = (int)std::max<long long>(1, std::min<long long>(max_tiles, (long long)oc.sms * oc.per_sm));
+
+  ProfRec rec{-1, nullptr, nullptr, 0.0};
+  if (p->profiling) {
+    char slot[32];
+    std::snprintf(slot, sizeof slot, "%s/L%d-%d", inverse ? "inv" : "fwd", k0, k1 - 1);
+    rec.slot = slot_of(p, slot);
+    rec.a = take_event(p);
+    rec.b = take_event(p);
+    rec.bytes = bytes;
+    cudaEventRecord(rec.a, s);
+  }
+  const cudaError_t e = call_tail(key, TailCall{&tp, blocks, s});
+  if (p->profiling) {
+    cudaEventRecord(rec.b, s);
+    p->pending.push_back(rec);
+  }
+  return from_cuda(e);
+}
+
+// The transform proper: levels in order (forward) or reverse (inverse), the
+// small ones in one fused-tail launch.
 dwt_status run(dwt_plan_s* p, bool inverse, const void* src, size_t src_pitch, void* dst,
                size_t dst_pitch, cudaStream_t s) {
   const size_t es = p->es;
@@ -903,76 +1074,35 @@ dwt_status run(dwt_plan_s* p, bool inverse, const void* src, size_t src_pitch, v
   }
   const Lifting L = lifting_of(p->wavelet);
   const int Lv = p->levels;
-  char slot[32];
   std::vector<void*> ll(p->ll);
   std::vector<size_t> llp(p->ll_pitch);
   ll.resize(Lv, nullptr);
   llp.resize(Lv, 0);
+  int k0, k1;
+  tail_range(p, scheme, inverse, &k0, &k1);
 
-  for (int step = 0; step < Lv; ++step) {
-    const int k = inverse ? Lv - 1 - step : step;
-    LevelArgs a{};
-    level_dims(p, k, a);
-    const LevelIO io = level_io(p, inverse, k, a, src, src_pitch, dst, dst_pitch, ll.data(), llp.data());
-    const void* const* band = io.band;
-    const long long* bpitch = io.bpitch;
-    const void* samples = io.samples;
-    const long long spitch = io.spitch;
-    const Coefs cf = make_coefs(L, p->norm, a.W, a.H, PASS_FUSED, inverse);
-    ConvTaps ct;
-    std::memset(&ct, 0, sizeof ct);
-    if (scheme == DWT_CONVOLUTION && !conv_taps(L, p->norm, a.W, a.H, inverse, &ct))
-      return DWT_EUNSUPPORTED;
-    dwt_status st;
-    if (scheme != DWT_ROWCOL) {
-      LaunchKey key{p->wavelet, p->dtype, scheme, PASS_FUSED, inverse ? 1 : 0,
-                    p->norm == DWT_NORM_JPEG2000 && a.W >= 2 && a.H >= 2 ? 1 : 0};
-      fused_io(io, inverse, a);
-      std::snprintf(slot, sizeof slot, "%s/L%d", inverse ? "inv" : "fwd", k);
-      st = launch(p, key, a, cf, ct, s, slot);
-    } else {
-      // row-column: vertical pass and horizontal pass through p->tmp
-      const long long tp = (long long)(p->tmp_pitch / es);
-      LevelArgs v = a, hz = a;
-      const Coefs cv = make_coefs(L, p->norm, a.W, a.H, PASS_VERT, inverse);
-      const Coefs chz = make_coefs(L, p->norm, a.W, a.H, PASS_HORZ, inverse);
-      LaunchKey kv{p->wavelet, p->dtype, DWT_ROWCOL, PASS_VERT, inverse ? 1 : 0};
-      LaunchKey kh{p->wavelet, p->dtype, DWT_ROWCOL, PASS_HORZ, inverse ? 1 : 0};
-      if (!inverse) {
-        v.src[0] = samples;
-        v.src_pitch[0] = spitch;
-        v.dst[0] = p->tmp;
-        v.dst_pitch[0] = tp;
-        hz.src[0] = p->tmp;
-        hz.src_pitch[0] = tp;
-        for (int i = 0; i < 4; ++i) {
-          hz.dst[i] = const_cast<void*>(band[i]);
-          hz.dst_pitch[i] = bpitch[i];
-        }
-        std::snprintf(slot, sizeof slot, "fwd-v/L%d", k);
-        st = launch(p, kv, v, cv, ct, s, slot);
-        if (st != DWT_OK) return st;
-        std::snprintf(slot, sizeof slot, "fwd-h/L%d", k);
-        st = launch(p, kh, hz, chz, ct, s, slot);
+  if (!inverse) {
+    for (int k = 0; k < Lv; ++k) {
+      dwt_status st;
+      if (k == k0) {
+        st = run_tail(p, false, k0, k1, scheme, L, src, src_pitch, dst, dst_pitch, ll.data(), llp.data(), s);
+        k = k1 - 1;
       } else {
-        for (int i = 0; i < 4; ++i) {
-          hz.src[i] = band[i];
-          hz.src_pitch[i] = bpitch[i];
-        }
-        hz.dst[0] = p->tmp;
-        hz.dst_pitch[0] = tp;
-        v.src[0] = p->tmp;
-        v.src_pitch[0] = tp;
-        v.dst[0] = const_cast<void*>(samples);
-        v.dst_pitch[0] = spitch;
-        std::snprintf(slot, sizeof slot, "inv-h/L%d", k);
-        st = launch(p, kh, hz, chz, ct, s, slot);
-        if (st != DWT_OK) return st;
-        std::snprintf(slot, sizeof slot, "inv-v/L%d", k);
-        st = launch(p, kv, v, cv, ct, s, slot);
+        st = run_level(p, false, k, scheme, L, src, src_pitch, dst, dst_pitch, ll.data(), llp.data(), s);
       }
+      if (st != DWT_OK) return st;
     }
-    if (st != DWT_OK) return st;
+  } else {
+    for (int k = Lv - 1; k >= 0; --k) {
+      dwt_status st;
+      if (k0 < k1 && k == k1 - 1) {
+        st = run_tail(p, true, k0, k1, scheme, L, src, src_pitch, dst, dst_pitch, ll.data(), llp.data(), s);
+        k = k0;
+      } else {
+        st = run_level(p, true, k, scheme, L, src, src_pitch, dst, dst_pitch, ll.data(), llp.data(), s);
+      }
+      if (st != DWT_OK) return st;
+    }
   }
   return DWT_OK;
 }
@@ -1470,6 +1600,20 @@ dwt_status dwt_plan_set_tile(dwt_plan p, int strip_rows, int stages) {
   p->strip_rows = strip_rows;
   p->nstages = stages ? stages : kDefaultStages;
   p->tile_set = strip_rows != 0 || stages != 0;
+  return DWT_OK;
+}
+
+dwt_status dwt_plan_set_fusion(dwt_plan p, long long max_pixels) {
+  if (!p || max_pixels < -1) return DWT_EINVAL;
+  std::lock_guard<std::mutex> lk(p->mu);
+  p->fuse_px = max_pixels;
+  return DWT_OK;
+}
+
+dwt_status dwt_plan_get_fusion(dwt_plan p, long long* max_pixels) {
+  if (!p || !max_pixels) return DWT_EINVAL;
+  std::lock_guard<std::mutex> lk(p->mu);
+  *max_pixels = p->fuse_px < 0 ? kDefaultFusePx : p->fuse_px;
   return DWT_OK;
 }
 

@@ -129,6 +129,53 @@ struct LaunchCall {
   cudaStream_t stream;
 };
 
+// ---- fused tail: several small levels of one image in one launch ----------
+// (tile_kernel.cuh).  Levels run in 2-D tiles in shared memory, with a grid
+// barrier between levels.
+constexpr int kMaxTailLevels = 12;
+constexpr int kTileThreads = 256;
+
+// One level of a fused tail: geometry and planes as for the streaming
+// kernels (the strip fields are unused), its coefficients, and its tiles.
+struct TileLevel {
+  LevelArgs a;
+  Coefs cf;
+  int ntx, nty;
+};
+
+struct TailParams {
+  TileLevel lv[kMaxTailLevels];  // in processing order
+  int nlevels;
+  unsigned* barrier;  // grid barrier counter (device memory, any value)
+};
+
+// Stored interior of a tile (quads), shared memory and entry of a kernel.
+struct TailInfo {
+  int inner_rows, inner_cols;
+  size_t smem_bytes;
+  const void* fn;
+};
+
+struct TailCall {
+  const TailParams* p;
+  int blocks;
+  cudaStream_t stream;
+};
+
+// Returns true when the group has a tail kernel for `k`; then fills *info
+// and/or launches.
+using TailFn = bool (*)(const LaunchKey& k, TailInfo* info, const TailCall* call, cudaError_t* err);
+
+bool tail_sweldens(const LaunchKey&, TailInfo*, const TailCall*, cudaError_t*);
+bool tail_iwahashi(const LaunchKey&, TailInfo*, const TailCall*, cudaError_t*);
+bool tail_iwahashi_s(const LaunchKey&, TailInfo*, const TailCall*, cudaError_t*);
+bool tail_explosive(const LaunchKey&, TailInfo*, const TailCall*, cudaError_t*);
+bool tail_explosive_s(const LaunchKey&, TailInfo*, const TailCall*, cudaError_t*);
+bool tail_monolithic(const LaunchKey&, TailInfo*, const TailCall*, cudaError_t*);
+bool tail_monolithic_s(const LaunchKey&, TailInfo*, const TailCall*, cudaError_t*);
+bool tail_polyphase(const LaunchKey&, TailInfo*, const TailCall*, cudaError_t*);
+bool tail_polyphase_s(const LaunchKey&, TailInfo*, const TailCall*, cudaError_t*);
+
 // Returns true when the group handles `k`; then fills *info and/or launches.
 using GroupFn = bool (*)(const LaunchKey& k, int nstages, KernelInfo* info, const LaunchCall* call,
                          cudaError_t* err);

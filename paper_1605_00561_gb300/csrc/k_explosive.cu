@@ -8,4 +8,8 @@ bool group_explosive(const LaunchKey& k, int ns, KernelInfo* info, const LaunchC
   return dev::fused_float<EXPLOSIVE, true>(k, ns, info, call, err);
 }
 
+bool tail_explosive(const LaunchKey& k, TailInfo* info, const TailCall* call, cudaError_t* err) {
+  return dev::tail_float<EXPLOSIVE>(k, info, call, err);
+}
+
 }  // namespace dwt

@@ -8,4 +8,8 @@ bool group_explosive_s(const LaunchKey& k, int ns, KernelInfo* info, const Launc
   return dev::fused_float<EXPLOSIVE_S, true>(k, ns, info, call, err);
 }
 
+bool tail_explosive_s(const LaunchKey& k, TailInfo* info, const TailCall* call, cudaError_t* err) {
+  return dev::tail_float<EXPLOSIVE_S>(k, info, call, err);
+}
+
 }  // namespace dwt

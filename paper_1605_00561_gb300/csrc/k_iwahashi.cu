@@ -8,4 +8,8 @@ bool group_iwahashi(const LaunchKey& k, int ns, KernelInfo* info, const LaunchCa
   return dev::fused_float<IWAHASHI, true>(k, ns, info, call, err);
 }
 
+bool tail_iwahashi(const LaunchKey& k, TailInfo* info, const TailCall* call, cudaError_t* err) {
+  return dev::tail_float<IWAHASHI>(k, info, call, err);
+}
+
 }  // namespace dwt

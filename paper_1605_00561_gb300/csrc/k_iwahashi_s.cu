@@ -8,4 +8,8 @@ bool group_iwahashi_s(const LaunchKey& k, int ns, KernelInfo* info, const Launch
   return dev::fused_float<IWAHASHI_S, true>(k, ns, info, call, err);
 }
 
+bool tail_iwahashi_s(const LaunchKey& k, TailInfo* info, const TailCall* call, cudaError_t* err) {
+  return dev::tail_float<IWAHASHI_S>(k, info, call, err);
+}
+
 }  // namespace dwt

@@ -8,4 +8,8 @@ bool group_monolithic(const LaunchKey& k, int ns, KernelInfo* info, const Launch
   return dev::fused_float<MONOLITHIC, true>(k, ns, info, call, err);
 }
 
+bool tail_monolithic(const LaunchKey& k, TailInfo* info, const TailCall* call, cudaError_t* err) {
+  return dev::tail_float<MONOLITHIC>(k, info, call, err);
+}
+
 }  // namespace dwt

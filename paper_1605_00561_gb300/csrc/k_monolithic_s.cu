@@ -8,4 +8,8 @@ bool group_monolithic_s(const LaunchKey& k, int ns, KernelInfo* info, const Laun
   return dev::fused_float<MONOLITHIC_S, true>(k, ns, info, call, err);
 }
 
+bool tail_monolithic_s(const LaunchKey& k, TailInfo* info, const TailCall* call, cudaError_t* err) {
+  return dev::tail_float<MONOLITHIC_S>(k, info, call, err);
+}
+
 }  // namespace dwt

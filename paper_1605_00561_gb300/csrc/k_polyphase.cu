@@ -8,4 +8,8 @@ bool group_polyphase(const LaunchKey& k, int ns, KernelInfo* info, const LaunchC
   return dev::fused_float<POLYPHASE, true>(k, ns, info, call, err);
 }
 
+bool tail_polyphase(const LaunchKey& k, TailInfo* info, const TailCall* call, cudaError_t* err) {
+  return dev::tail_float<POLYPHASE>(k, info, call, err);
+}
+
 }  // namespace dwt

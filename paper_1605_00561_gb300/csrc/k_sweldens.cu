@@ -17,4 +17,16 @@ bool group_sweldens(const LaunchKey& k, int ns, KernelInfo* info, const LaunchCa
   return false;
 }
 
+bool tail_sweldens(const LaunchKey& k, TailInfo* info, const TailCall* call, cudaError_t* err) {
+  if (k.pass == PASS_FUSED && k.scheme == SWELDENS && k.dtype == I32) {
+    if (k.wavelet != W53) return false;
+    // reversible 5/3 in the JPEG 2000 order; a tail level has both sides >= 2
+    return k.inverse ? dev::run_tail<dev::TailCfg<int, int, dev::IntFused<true>::type, SUBBANDS, SAMPLES,
+                                                  dev::StCoefs<W53, true>>>(info, call, err)
+                     : dev::run_tail<dev::TailCfg<int, int, dev::IntFused<false>::type, SAMPLES, SUBBANDS,
+                                                  dev::StCoefs<W53, false>>>(info, call, err);
+  }
+  return dev::tail_float<SWELDENS>(k, info, call, err);
+}
+
 }  // namespace dwt

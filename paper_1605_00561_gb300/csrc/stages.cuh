@@ -68,6 +68,25 @@ __device__ __forceinline__ V hpos(const V (&x)[QL]) {
 }
 
 // ---------------------------------------------------------------------------
+// Where a stage reads its inputs.  A stage evaluates one lane's QL quads;
+// it asks its accessor for subband S of the quad DY rows below and DX
+// columns right of the lane's quad J (all compile-time), and starts from
+// the lane's own pre-step values `own`.  WinAcc serves the streaming
+// kernels: vertical neighbours from the stage's window of rows (row UP is
+// the lane's own), horizontal ones by warp shuffles.  The tile kernels use
+// an accessor into a shared-memory plane (tile_kernel.cuh).  Both evaluate
+// every stage with the same arithmetic in the same order.
+// ---------------------------------------------------------------------------
+template <typename V, int QL, int UP>
+struct WinAcc {
+  const Row<V, QL>* w;
+  template <int S, int DY, int DX, int J>
+  __device__ __forceinline__ V at() const {
+    return hpos<J + DX>(w[UP + DY].s[S]);
+  }
+};
+
+// ---------------------------------------------------------------------------
 // 1-D operators
 // ---------------------------------------------------------------------------
 enum Op : int { OP_I, OP_P, OP_U, OP_P0, OP_P1, OP_U0, OP_U1, OP_V, OP_V1 };
@@ -215,8 +234,17 @@ struct Lin {
   // roundings at the magnitude of the target than one FMA per tap.  The
   // class holding the centre tap, whose coefficient is the largest in the
   // products of V, is accumulated in the second pass, after all others.
-  template <class T, bool CENTRE_PASS, int QL, class CS>
-  __device__ __forceinline__ static void term(const Row<float, QL>* w, Row<float, QL>& o, const CS& c) {
+  // Subbands this step reads at another quad's position (published by the
+  // tile kernels before the step): sources of terms that reach beyond the
+  // quad itself.  A step with none is local and needs no barrier.
+  static constexpr unsigned NEIGHBOUR_SRCS =
+      (0u | ... | ((OpShape<DEG, Ts::vop>::lo < 0 || OpShape<DEG, Ts::vop>::hi > 0 ||
+                    OpShape<DEG, Ts::hop>::lo < 0 || OpShape<DEG, Ts::hop>::hi > 0)
+                       ? (1u << Ts::src)
+                       : 0u));
+
+  template <class T, bool CENTRE_PASS, int QL, class A, class CS>
+  __device__ __forceinline__ static void term(const A& acc, Row<float, QL>& o, const CS& c) {
     using VS = OpShape<DEG, T::vop>;
     using HS = OpShape<DEG, T::hop>;
     static_for<0, VS::NCLS - 1>([&](auto cvi) {
@@ -233,13 +261,12 @@ struct Lin {
           static_for<VS::lo, VS::hi>([&](auto dy) {
             constexpr int DY = decltype(dy)::value;
             if constexpr (VS::has(DY) && VS::cls(DY) == CV) {
-              const float(&x)[QL] = w[UP + DY].s[T::src];
               static_for<HS::lo, HS::hi>([&](auto dx) {
                 constexpr int DX = decltype(dx)::value;
                 if constexpr (HS::has(DX) && HS::cls(DX) == CH) {
                   static_for<0, QL - 1>([&](auto jj) {
                     constexpr int J = decltype(jj)::value;
-                    const float v = hpos<J + DX>(x);
+                    const float v = acc.template at<T::src, DY, DX, J>();
                     s[J] = first ? v : s[J] + v;
                   });
                   first = false;
@@ -256,10 +283,10 @@ struct Lin {
     });
   }
 
-  template <int QL, class CS>
-  __device__ __forceinline__ static void eval(const Row<float, QL>* w, Row<float, QL>& o, const CS& c,
-                                              const ConvTaps&) {
-    o = w[UP];
+  template <int QL, class A, class CS>
+  __device__ __forceinline__ static void eval(const Row<float, QL>& own, const A& acc, Row<float, QL>& o,
+                                              const CS& c, const ConvTaps&) {
+    o = own;
     if constexpr (REPLACE) {
 #pragma unroll
       for (int s = 0; s < 4; ++s)
@@ -267,21 +294,22 @@ struct Lin {
 #pragma unroll
           for (int j = 0; j < QL; ++j) o.s[s][j] = 0.0f;
     }
-    (term<Ts, false, QL, CS>(w, o, c), ...);
-    (term<Ts, true, QL, CS>(w, o, c), ...);
+    (term<Ts, false, QL>(acc, o, c), ...);
+    (term<Ts, true, QL>(acc, o, c), ...);
   }
 };
 
 // Scaling step (Sec. 2.2, the diagonal matrix of M): per-subband factors.
 struct Scale {
   static constexpr int UP = 0, DOWN = 0, LEFT = 0, RIGHT = 0;
-  template <int QL, class CS>
-  __device__ __forceinline__ static void eval(const Row<float, QL>* w, Row<float, QL>& o, const CS& c,
-                                              const ConvTaps&) {
+  static constexpr unsigned NEIGHBOUR_SRCS = 0;
+  template <int QL, class A, class CS>
+  __device__ __forceinline__ static void eval(const Row<float, QL>& own, const A&, Row<float, QL>& o,
+                                              const CS& c, const ConvTaps&) {
 #pragma unroll
     for (int s = 0; s < 4; ++s)
 #pragma unroll
-      for (int j = 0; j < QL; ++j) o.s[s][j] = w[0].s[s][j] * c.scale(s);
+      for (int j = 0; j < QL; ++j) o.s[s][j] = own.s[s][j] * c.scale(s);
   }
 };
 
@@ -312,32 +340,32 @@ struct Conv {
   static constexpr int UP = -cmin(cmin(S::lo(0, 0), S::lo(0, 1)), cmin(S::lo(1, 0), S::lo(1, 1)));
   static constexpr int DOWN = cmax(cmax(S::hi(0, 0), S::hi(0, 1)), cmax(S::hi(1, 0), S::hi(1, 1)));
   static constexpr int LEFT = UP, RIGHT = DOWN;
+  static constexpr unsigned NEIGHBOUR_SRCS = 15u;
 
-  template <int QL, class CS>
-  __device__ __forceinline__ static void eval(const Row<float, QL>* w, Row<float, QL>& o, const CS&,
-                                              const ConvTaps& t) {
+  template <int QL, class A, class CS>
+  __device__ __forceinline__ static void eval(const Row<float, QL>&, const A& acc, Row<float, QL>& o,
+                                              const CS&, const ConvTaps& t) {
     static_for<0, 3>([&](auto so_sx) {
       constexpr int SO = decltype(so_sx)::value >> 1, SX = decltype(so_sx)::value & 1;
-      float acc[QL];
+      float sum[QL];
 #pragma unroll
-      for (int j = 0; j < QL; ++j) acc[j] = 0.0f;
+      for (int j = 0; j < QL; ++j) sum[j] = 0.0f;
       static_for<0, 3>([&](auto ti_tx) {
         constexpr int TI = decltype(ti_tx)::value >> 1, TX = decltype(ti_tx)::value & 1;
         static_for<S::lo(SO, TI), S::hi(SO, TI)>([&](auto dy) {
           constexpr int DY = decltype(dy)::value;
-          const float(&x)[QL] = w[UP + DY].s[2 * TI + TX];
           static_for<S::lo(SX, TX), S::hi(SX, TX)>([&](auto dx) {
             constexpr int DX = decltype(dx)::value;
             const float cf = t.t[SO][SX][TI][TX][DY + 2][DX + 2];
             static_for<0, QL - 1>([&](auto jj) {
               constexpr int J = decltype(jj)::value;
-              acc[J] = fmaf(cf, hpos<J + DX>(x), acc[J]);
+              sum[J] = fmaf(cf, acc.template at<2 * TI + TX, DY, DX, J>(), sum[J]);
             });
           });
         });
       });
 #pragma unroll
-      for (int j = 0; j < QL; ++j) o.s[2 * SO + SX][j] = acc[j];
+      for (int j = 0; j < QL; ++j) o.s[2 * SO + SX][j] = sum[j];
     });
   }
 };
@@ -355,48 +383,47 @@ struct Int53 {
   static constexpr int LEFT = KIND == 3 ? 1 : 0;
   static constexpr int RIGHT = KIND == 2 ? 1 : 0;
 
-  template <int QL, class CS>
-  __device__ __forceinline__ static void eval(const Row<int, QL>* w, Row<int, QL>& o, const CS& c,
-                                              const ConvTaps&) {
-    o = w[UP];
+  static constexpr unsigned NEIGHBOUR_SRCS = KIND == 0   ? (1u << LL) | (1u << HL)
+                                             : KIND == 1 ? (1u << LH) | (1u << HH)
+                                             : KIND == 2 ? (1u << LL) | (1u << LH)
+                                                         : (1u << HL) | (1u << HH);
+
+  template <int QL, class A, class CS>
+  __device__ __forceinline__ static void eval(const Row<int, QL>& own, const A& acc, Row<int, QL>& o,
+                                              const CS& c, const ConvTaps&) {
+    o = own;
     const int sg = INV ? -1 : 1;
     if constexpr (KIND == 0) {  // odd rows -= floor((even above + even below) / 2)
       if (c.v_on()) {
-#pragma unroll
-        for (int j = 0; j < QL; ++j) {
-          o.s[LH][j] -= sg * ((w[0].s[LL][j] + w[1].s[LL][j]) >> 1);
-          o.s[HH][j] -= sg * ((w[0].s[HL][j] + w[1].s[HL][j]) >> 1);
-        }
+        static_for<0, QL - 1>([&](auto jj) {
+          constexpr int J = decltype(jj)::value;
+          o.s[LH][J] -= sg * ((acc.template at<LL, 0, 0, J>() + acc.template at<LL, 1, 0, J>()) >> 1);
+          o.s[HH][J] -= sg * ((acc.template at<HL, 0, 0, J>() + acc.template at<HL, 1, 0, J>()) >> 1);
+        });
       }
     } else if constexpr (KIND == 1) {  // even rows += floor((odd above + odd below + 2) / 4)
       if (c.v_on()) {
-#pragma unroll
-        for (int j = 0; j < QL; ++j) {
-          o.s[LL][j] += sg * ((w[0].s[LH][j] + w[1].s[LH][j] + 2) >> 2);
-          o.s[HL][j] += sg * ((w[0].s[HH][j] + w[1].s[HH][j] + 2) >> 2);
-        }
+        static_for<0, QL - 1>([&](auto jj) {
+          constexpr int J = decltype(jj)::value;
+          o.s[LL][J] += sg * ((acc.template at<LH, -1, 0, J>() + acc.template at<LH, 0, 0, J>() + 2) >> 2);
+          o.s[HL][J] += sg * ((acc.template at<HH, -1, 0, J>() + acc.template at<HH, 0, 0, J>() + 2) >> 2);
+        });
       }
     } else if constexpr (KIND == 2) {  // odd columns from the even ones at m, m+1
       if (c.h_on()) {
-        const int llr = hpos<QL>(w[0].s[LL]), lhr = hpos<QL>(w[0].s[LH]);
-#pragma unroll
-        for (int j = 0; j < QL; ++j) {
-          const int lln = j + 1 < QL ? w[0].s[LL][j + 1] : llr;
-          const int lhn = j + 1 < QL ? w[0].s[LH][j + 1] : lhr;
-          o.s[HL][j] -= sg * ((w[0].s[LL][j] + lln) >> 1);
-          o.s[HH][j] -= sg * ((w[0].s[LH][j] + lhn) >> 1);
-        }
+        static_for<0, QL - 1>([&](auto jj) {
+          constexpr int J = decltype(jj)::value;
+          o.s[HL][J] -= sg * ((acc.template at<LL, 0, 0, J>() + acc.template at<LL, 0, 1, J>()) >> 1);
+          o.s[HH][J] -= sg * ((acc.template at<LH, 0, 0, J>() + acc.template at<LH, 0, 1, J>()) >> 1);
+        });
       }
     } else {  // even columns from the odd ones at m-1, m
       if (c.h_on()) {
-        const int hll = hpos<-1>(w[0].s[HL]), hhl = hpos<-1>(w[0].s[HH]);
-#pragma unroll
-        for (int j = 0; j < QL; ++j) {
-          const int hlp = j > 0 ? w[0].s[HL][j - 1] : hll;
-          const int hhp = j > 0 ? w[0].s[HH][j - 1] : hhl;
-          o.s[LL][j] += sg * ((hlp + w[0].s[HL][j] + 2) >> 2);
-          o.s[LH][j] += sg * ((hhp + w[0].s[HH][j] + 2) >> 2);
-        }
+        static_for<0, QL - 1>([&](auto jj) {
+          constexpr int J = decltype(jj)::value;
+          o.s[LL][J] += sg * ((acc.template at<HL, 0, -1, J>() + acc.template at<HL, 0, 0, J>() + 2) >> 2);
+          o.s[LH][J] += sg * ((acc.template at<HH, 0, -1, J>() + acc.template at<HH, 0, 0, J>() + 2) >> 2);
+        });
       }
     }
   }
@@ -462,7 +489,7 @@ struct Pipe<V, QL, List<S0, S...>> {
     for (int k = 0; k + 1 < NW; ++k) win[k] = win[k + 1];
     win[NW - 1] = r;
     Row<V, QL> o;
-    S0::template eval<QL>(win, o, c, t);
+    S0::template eval<QL>(win[S0::UP], WinAcc<V, QL, S0::UP>{win}, o, c, t);
     return rest.push(o, c, t);
   }
 };

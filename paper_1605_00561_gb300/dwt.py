@@ -17,7 +17,7 @@ __all__ = [
     "DWT_OK", "DWT_EINVAL", "DWT_ENOMEM", "DWT_EUNSUPPORTED", "DWT_ECUDA", "DWT_ETIMEOUT", "DWT_EBUSY",
     "DWT_CDF53", "DWT_CDF97", "DWT_DD137", "DWT_F32", "DWT_F16S", "DWT_I32",
     "SCHEMES", "DWT_NORM_JPEG2000", "DWT_NORM_ZETA",
-    "dwt_plan_create", "dwt_plan_set_scheme", "dwt_plan_set_tile", "dwt_plan_get_tile", "dwt_plan_get_scheme", "dwt_plan_set_normalization",
+    "dwt_plan_create", "dwt_plan_set_scheme", "dwt_plan_set_tile", "dwt_plan_set_fusion", "dwt_plan_get_fusion", "dwt_plan_get_tile", "dwt_plan_get_scheme", "dwt_plan_set_normalization",
     "dwt2_forward", "dwt2_inverse", "dwt2_forward_noalloc", "dwt2_forward_host", "dwt2_inverse_host", "dwt_batch_submit",
     "dwt_plan_device_status", "dwt_noalloc_device_status", "dwt_set_wait_limits", "dwt_debug_inject",
     "DWT_INJECT_NONE", "DWT_INJECT_ENOMEM", "DWT_INJECT_HOLD", "DWT_INJECT_BATCH_DEP", "dwt_plan_set_profiling", "dwt_plan_read_profile", "dwt_plan_autotune",
@@ -65,6 +65,8 @@ EXPORTS = {
     "dwt_plan_get_tile": ([ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)],
                           ctypes.c_int),
     "dwt_plan_set_normalization": ([ctypes.c_void_p, ctypes.c_int], ctypes.c_int),
+    "dwt_plan_set_fusion": ([ctypes.c_void_p, ctypes.c_longlong], ctypes.c_int),
+    "dwt_plan_get_fusion": ([ctypes.c_void_p, ctypes.POINTER(ctypes.c_longlong)], ctypes.c_int),
     "dwt2_forward": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_size_t,
                       ctypes.c_void_p], ctypes.c_int),
     "dwt2_inverse": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_size_t,
@@ -141,6 +143,18 @@ def dwt_plan_get_tile(plan: int):
     r, st = ctypes.c_int(), ctypes.c_int()
     _check(lib().dwt_plan_get_tile(plan, ctypes.byref(r), ctypes.byref(st)), "dwt_plan_get_tile")
     return r.value, st.value
+
+
+def dwt_plan_set_fusion(plan: int, max_pixels: int = -1) -> None:
+    """Levels whose input has at most max_pixels samples run in one fused
+    launch (-1: default, 0: off)."""
+    _check(lib().dwt_plan_set_fusion(plan, max_pixels), "dwt_plan_set_fusion")
+
+
+def dwt_plan_get_fusion(plan: int) -> int:
+    v = ctypes.c_longlong()
+    _check(lib().dwt_plan_get_fusion(plan, ctypes.byref(v)), "dwt_plan_get_fusion")
+    return v.value
 
 
 def dwt_plan_get_scheme(plan: int) -> int:

@@ -72,8 +72,12 @@ def test_batch_row_wait_times_out_and_reports(dwt):
         p.close()
 
 
+@pytest.mark.parametrize("fusion", [-1, 0])
 @pytest.mark.parametrize("dtype", ["f32", "i32"])
-def test_plan_wait_times_out_and_reports(dwt, dtype):
+def test_plan_wait_times_out_and_reports(dwt, dtype, fusion):
+    """With the default fusion the whole pyramid is one fused-tail launch
+    (the hold is CTA 0 of its first level); without it, one streaming launch
+    per level (the hold is the second level's first strip)."""
     h, w, L = 257, 390, 3
     if dtype == "i32":
         x = inputs.int12_image(h, w, seed=3)
@@ -83,12 +87,13 @@ def test_plan_wait_times_out_and_reports(dwt, dtype):
         x = inputs.uniform_image(h, w, seed=3)
         ref = oracle.dwt2(x.astype(np.float64), oracle.CDF97, L)
         plan = dwt.Plan(w, h, "cdf97", L, "f32")
+    dwt.dwt_plan_set_fusion(plan.handle, fusion)
     xd = torch.from_numpy(x).cuda()
     c = torch.empty_like(xd)
     plan.forward(xd, c)  # first call: the plan's allocations
     assert dwt.dwt_plan_device_status(plan.handle) == dwt.DWT_OK
     dwt.dwt_set_wait_limits(0, SHORT_SPINS)
-    dwt.dwt_debug_inject(dwt.DWT_INJECT_HOLD, 1, 1)  # the second level's launch holds
+    dwt.dwt_debug_inject(dwt.DWT_INJECT_HOLD, 0 if fusion else 1, 1)
     plan.forward(xd, c)
     assert dwt.dwt_plan_device_status(plan.handle) == dwt.DWT_ETIMEOUT
     # the query cleared the word; the next call is clean and correct
