@@ -206,10 +206,12 @@ __device__ __forceinline__ float op_tap(const CS& c) {
     return u1;
   } else if constexpr (OP == OP_V) {  // V = PU + 1: pu z^-1 + (1 + 2pu) + pu z
     static_assert(DEG == 1, "V of degree 3 reaches beyond one lane");
-    return OFF == 0 ? 1.0f + 2.0f * p1 * u1 : p1 * u1;
+    // rounded products and sums (no contraction into an FMA), so that
+    // every kernel folds the same coefficient whatever its inlining context
+    return OFF == 0 ? __fadd_rn(1.0f, __fmul_rn(__fmul_rn(2.0f, p1), u1)) : __fmul_rn(p1, u1);
   } else {  // OP_V1 = P1 U1 + 1 = 1 + pu (degree 1)
     static_assert(DEG == 1, "V1 of degree 3 reaches beyond one lane");
-    return 1.0f + p1 * u1;
+    return __fadd_rn(1.0f, __fmul_rn(p1, u1));
   }
 }
 

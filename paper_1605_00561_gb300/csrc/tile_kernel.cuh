@@ -268,7 +268,7 @@ __global__ void __launch_bounds__(kTileThreads) tail_kernel(const __grid_constan
   using VT = typename C::VT;
   using G = TileGeom<typename C::PROG, C::QL>;
   constexpr int QL = G::QL;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   VT* xb = reinterpret_cast<VT*>(smem_raw);
   // the padding is never written by a step: zero it once (its values only
   // reach discarded halo quads, but they stay deterministic)

@@ -34,6 +34,13 @@ def dwt():
     return d
 
 
+def same(a, b, what):
+    if not torch.equal(a, b):
+        d = float((a.double() - b.double()).abs().max())
+        n = int((a != b).sum())
+        raise AssertionError(f"{what}: fused and unfused differ at {n} values, max |diff| {d:.3e}")
+
+
 def fwd_inv(dwt, x, wavelet, levels, dtype, scheme, fusion, zeta=False):
     h, w = x.shape
     plan = dwt.Plan(w, h, wavelet, levels, dtype, scheme=scheme)
@@ -59,7 +66,8 @@ def test_fused_equals_unfused_and_oracle(dwt, scheme, wavelet, h, w, L):
     x = inputs.uniform_image(h, w, seed=h + 3 * w)
     cf, yf = fwd_inv(dwt, x, wavelet, L, "f32", scheme, -1)
     cu, yu = fwd_inv(dwt, x, wavelet, L, "f32", scheme, 0)
-    assert torch.equal(cf, cu) and torch.equal(yf, yu)
+    same(cf, cu, "forward")
+    same(yf, yu, "inverse")
     ref = oracle.dwt2(x.astype(np.float64), OID[wavelet], L)
     assert np.abs(cf.cpu().numpy() - ref).max() <= TOL_F32
     assert float((yf - torch.from_numpy(x).cuda()).abs().max()) <= 2 * TOL_F32
@@ -71,7 +79,8 @@ def test_fused_dd137(dwt, scheme):
     x = inputs.uniform_image(h, w, seed=9)
     cf, yf = fwd_inv(dwt, x, "dd137", L, "f32", scheme, -1)
     cu, yu = fwd_inv(dwt, x, "dd137", L, "f32", scheme, 0)
-    assert torch.equal(cf, cu) and torch.equal(yf, yu)
+    same(cf, cu, "forward")
+    same(yf, yu, "inverse")
     ref = oracle.dwt2(x.astype(np.float64), oracle.DD137, L)
     assert np.abs(cf.cpu().numpy() - ref).max() <= TOL_F32
 
@@ -91,10 +100,11 @@ def test_fused_float16_storage_and_zeta(dwt, wavelet):
     x = inputs.uniform_image(h, w, seed=11)
     cf, yf = fwd_inv(dwt, x, wavelet, L, "f16s", "monolithic*", -1)
     cu, yu = fwd_inv(dwt, x, wavelet, L, "f16s", "monolithic*", 0)
-    assert torch.equal(cf, cu) and torch.equal(yf, yu)
+    same(cf, cu, "forward")
+    same(yf, yu, "inverse")
     zf, zy = fwd_inv(dwt, x, wavelet, L, "f32", "monolithic*", -1, zeta=True)
     zu, _ = fwd_inv(dwt, x, wavelet, L, "f32", "monolithic*", 0, zeta=True)
-    assert torch.equal(zf, zu)
+    same(zf, zu, "forward, zeta")
     ref = oracle.dwt2(x.astype(np.float64), OID[wavelet], L, norm=oracle.NORM_ZETA)
     assert np.abs(zf.cpu().numpy() - ref).max() <= TOL_F32 + 2e-5 * float(np.abs(ref).max())
 
