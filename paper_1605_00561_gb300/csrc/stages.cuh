@@ -308,10 +308,13 @@ struct Scale {
   template <int QL, class A, class CS>
   __device__ __forceinline__ static void eval(const Row<float, QL>& own, const A&, Row<float, QL>& o,
                                               const CS& c, const ConvTaps&) {
+    // a rounded product: never contracted into the next step's sums (which
+    // would make the result depend on how a kernel passes values between
+    // steps, in registers or through shared memory)
 #pragma unroll
     for (int s = 0; s < 4; ++s)
 #pragma unroll
-      for (int j = 0; j < QL; ++j) o.s[s][j] = own.s[s][j] * c.scale(s);
+      for (int j = 0; j < QL; ++j) o.s[s][j] = __fmul_rn(own.s[s][j], c.scale(s));
   }
 };
 
