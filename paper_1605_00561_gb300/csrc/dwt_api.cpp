@@ -409,8 +409,14 @@ constexpr int kBatchStripRows = 48;
 constexpr int kMaxSide = 1 << 28;
 
 // Levels whose input has at most this many samples run in the fused tail
-// (tile_kernel.cuh) by default: one launch for all of them.
-constexpr long long kDefaultFusePx = 2048LL * 2048LL;
+// (tile_kernel.cuh) by default: one launch for all of them.  Measured on
+// one 9/7 level alone, the tile kernel beats the streaming kernel up to
+// 512 x 512 (5.7 against 6.2 us forward, 6.2 against 7.9 inverse) and loses
+// from 1024 x 1024 (forward 8.2 against 7.4 us) and 2048 x 2048 (18.5
+// against 10.8 us), where it is bound by instruction issue with a tile's
+// halo recomputed; each fused level costs about 4.6 us (a grid barrier
+// and one tile's chain of steps) against 6-8 us per streaming launch.
+constexpr long long kDefaultFusePx = 512LL * 512LL;
 
 // Quad rows per strip.  Strips of about ten rows keep several waves of
 // one-warp blocks in flight, so the block scheduler balances SMs that

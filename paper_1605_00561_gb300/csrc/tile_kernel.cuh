@@ -48,17 +48,33 @@ struct TileGeom {
   static_assert(IR > 0 && IC > 0, "halo wider than the tile");
 };
 
+// One element of a 16-byte shared-memory vector of 4-byte values.
+template <typename V>
+__device__ __forceinline__ V lane_of(const int4& q, int k) {
+  const int b = k == 0 ? q.x : k == 1 ? q.y : k == 2 ? q.z : q.w;
+  if constexpr (std::is_integral<V>::value) return b;
+  else return __int_as_float(b);
+}
+
 // Accessor of a tile step: the thread's own quads from registers, the
 // others from the published plane (p points at the slot's first quad in
-// plane 0).
+// plane 0).  A neighbouring row over the slot's own columns is read as one
+// 16-byte vector (identical vector reads of a step are merged), the columns
+// beyond the slot one by one.
 template <typename V, int QL, int RS, int PS>
 struct TileAcc {
   const Row<V, QL>& own;
   const V* p;
   template <int S, int DY, int DX, int J>
   __device__ __forceinline__ V at() const {
-    if constexpr (DY == 0 && J + DX >= 0 && J + DX < QL) return own.s[S][J + DX];
-    else return p[S * PS + DY * RS + J + DX];
+    if constexpr (DY == 0 && J + DX >= 0 && J + DX < QL) {
+      return own.s[S][J + DX];
+    } else if constexpr (sizeof(V) == 4 && QL == 4 && J + DX >= 0 && J + DX < QL) {
+      const int4 q = *reinterpret_cast<const int4*>(p + S * PS + DY * RS);
+      return lane_of<V>(q, J + DX);
+    } else {
+      return p[S * PS + DY * RS + J + DX];
+    }
   }
 };
 
@@ -251,7 +267,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned* ctr, uint32_t limit, int*
         atomicOr(status, 1);
         break;
       }
-      __nanosleep(32);
+      if (spins >= 256) __nanosleep(32);  // a short spin first: most crossings complete within it
     }
     __threadfence();
     ok_sh = ok;
@@ -264,7 +280,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned* ctr, uint32_t limit, int*
 static __constant__ ConvTaps kTileNoTaps;
 
 template <class C>
-__global__ void __launch_bounds__(kTileThreads) tail_kernel(const __grid_constant__ TailParams P) {
+__global__ void __launch_bounds__(kTileThreads, 4) tail_kernel(const __grid_constant__ TailParams P) {
   using VT = typename C::VT;
   using G = TileGeom<typename C::PROG, C::QL>;
   constexpr int QL = G::QL;
@@ -301,11 +317,23 @@ __global__ void __launch_bounds__(kTileThreads) tail_kernel(const __grid_constan
       __syncthreads();
       if (held) ntiles = 0;
     }
+    // the first tile's inputs, then each tile's computation overlaps the
+    // loads of the CTA's next tile of the level
+    Row<VT, QL> next;
+    if ((int)blockIdx.x < ntiles) {
+      const int ty = blockIdx.x / L.ntx, tx = blockIdx.x - ty * L.ntx;
+      next = tile_load<C, QL>(a, ty * G::IR - G::UP + r, tx * G::IC - G::LEFT + c0);
+    }
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
       const int ty = t / L.ntx, tx = t - ty * L.ntx;
       const int qy = ty * G::IR - G::UP + r;
       const int qx0 = tx * G::IC - G::LEFT + c0;
-      Row<VT, QL> st = tile_load<C, QL>(a, qy, qx0);
+      Row<VT, QL> st = next;
+      const int tn = t + gridDim.x;
+      if (tn < ntiles) {
+        const int nty = tn / L.ntx, ntx = tn - nty * L.ntx;
+        next = tile_load<C, QL>(a, nty * G::IR - G::UP + r, ntx * G::IC - G::LEFT + c0);
+      }
       TileSteps<G, VT, typename C::PROG>::run(st, xb, slot_off, cur, coefs, kTileNoTaps);
       // interior rows and columns of the tile
       if (r >= G::UP && r < G::UP + G::IR && qy < a.ch) {

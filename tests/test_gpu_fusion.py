@@ -111,15 +111,22 @@ def test_fused_float16_storage_and_zeta(dwt, wavelet):
 
 def test_fusion_threshold_and_profile(dwt):
     """The default threshold fuses every level whose input has at most
-    2048 x 2048 samples: an 8192^2 six-level plan runs L0 and L1 one launch
-    each and L2-L5 in one launch; 0 turns the fusion off."""
+    512 x 512 samples: an 8192^2 six-level plan runs L0-L3 one launch each
+    and L4-L5 in one launch; a larger threshold fuses more; 0 turns the
+    fusion off."""
     n, L = 8192, 6
     plan = dwt.Plan(n, n, "cdf97", L, "f32", scheme="monolithic*")
-    assert dwt.dwt_plan_get_fusion(plan.handle) == 2048 * 2048
+    assert dwt.dwt_plan_get_fusion(plan.handle) == 512 * 512
     x = torch.rand(n, n, device="cuda")
     c = torch.empty_like(x)
     y = torch.empty_like(x)
     dwt.dwt_plan_set_profiling(plan.handle, True)
+    plan.forward(x, c)
+    plan.inverse(c, y)
+    names = [p["name"] for p in dwt.dwt_plan_read_profile(plan.handle)]
+    assert names == ["fwd/L0", "fwd/L1", "fwd/L2", "fwd/L3", "fwd/L4-5", "inv/L4-5", "inv/L3", "inv/L2",
+                     "inv/L1", "inv/L0"]
+    dwt.dwt_plan_set_fusion(plan.handle, 2048 * 2048)
     plan.forward(x, c)
     plan.inverse(c, y)
     names = [p["name"] for p in dwt.dwt_plan_read_profile(plan.handle)]

@@ -330,6 +330,7 @@ def test_host_buffer_entry_points(dwt):
 def test_profiling_reports_every_level(dwt):
     h, w, L = 256, 256, 3
     plan = dwt.Plan(w, h, "cdf97", L, "f32", scheme="monolithic*")
+    dwt.dwt_plan_set_fusion(plan.handle, 0)  # one launch per level
     dwt.dwt_plan_set_profiling(plan.handle, True)
     x = torch.rand(h, w, device="cuda")
     c = torch.empty_like(x)
