@@ -782,6 +782,9 @@ def main():
                 else "fallback 6.8 TB/s",
                 "timing": "CUDA events around each launch, profiled pass of the same steps after the timed region"}
     per_kernel = {p["name"]: round(p["total_ms"] / p["launches"] * 1e3, 2) for p in prof}
+    # every launch of the plan's kernels, counted from the profiled pass (the
+    # fused tail runs several levels in one launch)
+    launches_per_step = sum(p["launches"] for p in prof) // a.steps
 
     # The same level-0 kernel launched back to back (a one-level plan of the
     # same image and scheme): its steady-state duration without the events
@@ -870,7 +873,7 @@ def main():
                        "scheme": a.scheme, "l2": "inputs (268 MB per buffer) larger than L2, no flush",
                        "parallelism": f"replicas x{world}"},
             "roofline": roofline, "per_launch_us": per_kernel, "cpu_baseline": cpu, "e2e": e2e,
-            "clocks": clocks, "gpu_launches": 2 * L * a.steps,
+            "clocks": clocks, "gpu_launches": launches_per_step * a.steps,
         }), flush=True)
     plan.close()
     if world > 1:
