@@ -66,8 +66,8 @@ typedef enum {
 typedef enum {
   DWT_CDF53 = 0, /* P = -1/2 (1 + z^-1), U = 1/4 (1 + z) (Sec. 5)                  */
   DWT_CDF97 = 1, /* two pairs (alpha, beta), (gamma, delta) (Sec. 5)              */
-  DWT_DD137 = 2  /* Deslauriers-Dubuc 13/7: degree-3 P and U (Sec. 5); float32, all
-                    schemes but Polyphase(*) and Convolution                       */
+  DWT_DD137 = 2  /* Deslauriers-Dubuc 13/7: degree-3 P and U (Sec. 5); float32, every
+                    scheme                                                         */
 } dwt_wavelet;
 
 typedef enum {

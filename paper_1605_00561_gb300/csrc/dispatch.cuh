@@ -33,21 +33,22 @@ constexpr int kQuadsPerLane = (SCHEME == CONVOLUTION || (SCHEME == POLYPHASE && 
 // or degree-3 steps and for the unstarred Polyphase with two pairs, which
 // need them at four quadruples per lane (DD 13/7 runs 1.3-2.2x faster at 12
 // than squeezed into 128 registers; Polyphase 9/7 at four quadruples and 12
-// warps is 8-16 % faster at 8192^2 than at two and 16); 8 for Convolution.
+// warps is 8-16 % faster at 8192^2 than at two and 16); 8 for Convolution
+// and for Polyphase(*) with DD 13/7, whose merged steps are 7 x 7 stencils.
 template <int SCHEME, int WL>
 constexpr int kMinWarps =
     SCHEME == CONVOLUTION ? 8
+    : ((SCHEME == POLYPHASE || SCHEME == POLYPHASE_S) && WL == WDD) ? 8
     : (SCHEME == POLYPHASE && WL == W97) ? 12
     : ((WL == W97 || WL == WDD) &&
        (SCHEME == IWAHASHI || SCHEME == IWAHASHI_S || SCHEME == EXPLOSIVE || SCHEME == EXPLOSIVE_S))
         ? 12
         : 16;
 
-// Schemes whose steps stay stencils of the lifting operators themselves and
-// so take the degree-3 DD 13/7 pair; Polyphase and Convolution would need
-// the degree-6 products.
+// Every scheme takes the degree-3 DD 13/7 pair (Polyphase and Convolution
+// with the degree-6 products of P and U).
 template <int SCHEME>
-constexpr bool kHasDegree3 = SCHEME != POLYPHASE && SCHEME != POLYPHASE_S && SCHEME != CONVOLUTION;
+constexpr bool kHasDegree3 = true;
 
 // STATIC: coefficients folded in at compile time (StCoefs), for levels with
 // JPEG 2000 normalisation and both axes longer than one sample.
@@ -106,7 +107,8 @@ inline bool run_tail(TailInfo* info, const TailCall* call, cudaError_t* err) {
 
 template <int SCHEME, int WL, typename ST, bool INV, bool STATIC>
 using TailFusedCfg = TailCfg<ST, float, typename FusedProgram<SCHEME, WL, INV>::type, INV ? SUBBANDS : SAMPLES,
-                             INV ? SAMPLES : SUBBANDS, std::conditional_t<STATIC, StCoefs<WL, INV>, RtTag>>;
+                             INV ? SAMPLES : SUBBANDS, std::conditional_t<STATIC, StCoefs<WL, INV>, RtTag>,
+                             (SCHEME == POLYPHASE || SCHEME == POLYPHASE_S) ? 2 : 4>;
 
 template <int SCHEME, int WL, typename ST, bool STATIC>
 inline bool tail_dir(bool inv, TailInfo* info, const TailCall* call, cudaError_t* err) {

@@ -180,18 +180,19 @@ bool conv_taps(const Lifting& L, int norm, int Wk, int Hk, bool inverse, ConvTap
   Poly v[2][2], h[2][2];
   polyphase_1d(L, norm, Hk > 1, inverse, v);
   polyphase_1d(L, norm, Wk > 1, inverse, h);
+  constexpr int R = kConvReach, N = 2 * kConvReach + 1;
   for (int a = 0; a < 2; ++a)
     for (int b = 0; b < 2; ++b)
       for (int i = 0; i < 9; ++i)
-        if ((i < 2 || i > 6) && (std::fabs(v[a][b].c[i]) > 1e-12 || std::fabs(h[a][b].c[i]) > 1e-12))
-          return false;  // reach beyond the kernel's two quads
+        if ((i < 4 - R || i > 4 + R) && (std::fabs(v[a][b].c[i]) > 1e-12 || std::fabs(h[a][b].c[i]) > 1e-12))
+          return false;  // reach beyond the kernel's tap table
   for (int so = 0; so < 2; ++so)
     for (int sx = 0; sx < 2; ++sx)
       for (int ti = 0; ti < 2; ++ti)
         for (int tx = 0; tx < 2; ++tx)
-          for (int dy = 0; dy < 5; ++dy)
-            for (int dx = 0; dx < 5; ++dx)
-              t->t[so][sx][ti][tx][dy][dx] = (float)(v[so][ti].c[dy + 2] * h[sx][tx].c[dx + 2]);
+          for (int dy = 0; dy < N; ++dy)
+            for (int dx = 0; dx < N; ++dx)
+              t->t[so][sx][ti][tx][dy][dx] = (float)(v[so][ti].c[dy + 4 - R] * h[sx][tx].c[dx + 4 - R]);
   return true;
 }
 
@@ -601,11 +602,8 @@ int default_scheme(const dwt_plan_s* p) {
 bool scheme_supported(int wavelet, int dtype, int scheme) {
   if (scheme <= DWT_AUTO || scheme >= NUM_SCHEMES) return false;
   if (dtype == DWT_I32) return wavelet == DWT_CDF53 && (scheme == DWT_ROWCOL || scheme == DWT_SWELDENS);
-  // DD 13/7 (degree-3 pairs): float32, and only the schemes whose steps are
-  // stencils of P and U themselves (Polyphase and Convolution would need
-  // the degree-6 products)
-  if (wavelet == DWT_DD137)
-    return dtype == DWT_F32 && scheme != DWT_POLYPHASE && scheme != DWT_POLYPHASE_S && scheme != DWT_CONVOLUTION;
+  // DD 13/7 (degree-3 pairs): float32, every scheme
+  if (wavelet == DWT_DD137) return dtype == DWT_F32;
   return true;
 }
 

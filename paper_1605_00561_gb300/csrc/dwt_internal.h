@@ -63,11 +63,13 @@ struct Coefs {
 };
 
 // 2-D taps of the Convolution scheme, indexed
-// [out row type][out col type][in row type][in col type][dy + 2][dx + 2].
+// [out row type][out col type][in row type][in col type][dy + 3][dx + 3]
+// (quad offsets -3..3: DD 13/7 reaches 3 quads, the CDF wavelets 2).
 // Forward: out types are (L, H) bands, in types (even, odd) polyphase
 // components; inverse: the other way round.  Scaling is folded in.
+constexpr int kConvReach = 3;
 struct ConvTaps {
-  float t[2][2][2][2][5][5];
+  float t[2][2][2][2][2 * kConvReach + 1][2 * kConvReach + 1];
 };
 
 // Geometry and buffers of one launch (one level, one pass).

@@ -57,14 +57,16 @@ struct Row {
 };
 
 // The value of the quad at position P, where 0..QL-1 are this lane's quads,
-// negative positions the previous lane's last ones and QL.. the next lane's
-// first ones.
+// negative positions the previous lanes' and QL.. the next lanes' (one or
+// two lanes away).
 template <int P, typename V, int QL>
 __device__ __forceinline__ V hpos(const V (&x)[QL]) {
-  static_assert(P >= -QL && P < 2 * QL, "horizontal reach beyond the neighbouring lane");
+  static_assert(P >= -2 * QL && P < 3 * QL, "horizontal reach beyond two lanes");
   if constexpr (P >= 0 && P < QL) return x[P];
-  else if constexpr (P < 0) return __shfl_up_sync(kFull, x[QL + P], 1);
-  else return __shfl_down_sync(kFull, x[P - QL], 1);
+  else if constexpr (P >= -QL && P < 0) return __shfl_up_sync(kFull, x[QL + P], 1);
+  else if constexpr (P < 0) return __shfl_up_sync(kFull, x[2 * QL + P], 2);
+  else if constexpr (P < 2 * QL) return __shfl_down_sync(kFull, x[P - QL], 1);
+  else return __shfl_down_sync(kFull, x[P - 2 * QL], 2);
 }
 
 // ---------------------------------------------------------------------------
@@ -93,40 +95,52 @@ enum Op : int { OP_I, OP_P, OP_U, OP_P0, OP_P1, OP_U0, OP_U1, OP_V, OP_V1 };
 
 // Degree-1 lifting (CDF 5/3 and 9/7): P = p(1 + z), U = u(1 + z^-1) in the
 // quad-offset convention above.  Degree 3 (DD 13/7): P has taps p1 at 0, +1
-// and p3 at -1, +2; U has u1 at -1, 0 and u3 at -2, +1.
+// and p3 at -1, +2; U has u1 at -1, 0 and u3 at -2, +1.  V = PU + 1 (the
+// Polyphase scheme's diagonal operator, Sec. 2.3) spans -1..1 for degree 1
+// and -3..3 for degree 3; V1 = P1 U1 + 1 (Polyphase*) is the single tap
+// 1 + pu for degree 1 and spans -3..3 for degree 3.
 template <int DEG, int OP>
 struct OpShape {
-  static constexpr int lo = (OP == OP_I || OP == OP_P0 || OP == OP_U0 || OP == OP_V1) ? 0
+  static constexpr int lo = (OP == OP_I || OP == OP_P0 || OP == OP_U0) ? 0
+                            : (OP == OP_V1) ? (DEG == 1 ? 0 : -3)
                             : (OP == OP_P)  ? (DEG == 1 ? 0 : -1)
                             : (OP == OP_P1) ? (DEG == 1 ? 1 : -1)
                             : (OP == OP_U)  ? (DEG == 1 ? -1 : -2)
                             : (OP == OP_U1) ? (DEG == 1 ? -1 : -2)
-                                            : -1;  // OP_V (degree 1)
-  static constexpr int hi = (OP == OP_I || OP == OP_P0 || OP == OP_U0 || OP == OP_V1) ? 0
+                                            : (DEG == 1 ? -1 : -3);  // OP_V
+  static constexpr int hi = (OP == OP_I || OP == OP_P0 || OP == OP_U0) ? 0
+                            : (OP == OP_V1) ? (DEG == 1 ? 0 : 3)
                             : (OP == OP_P)  ? (DEG == 1 ? 1 : 2)
                             : (OP == OP_P1) ? (DEG == 1 ? 1 : 2)
                             : (OP == OP_U)  ? (DEG == 1 ? 0 : 1)
                             : (OP == OP_U1) ? (DEG == 1 ? -1 : 1)
-                                            : 1;
+                                            : (DEG == 1 ? 1 : 3);  // OP_V
   // The split operators P1, U1 of degree 3 have a zero tap at offset 0.
   __host__ __device__ static constexpr bool has(int off) {
     return !((OP == OP_P1 || OP == OP_U1) && DEG == 3 && off == 0);
   }
   // Taps with equal coefficients form a class: P and U have one class of
   // two taps (degree 1) or two classes (degree 3: distance 1 and 3); V has
-  // its centre 1 + 2pu and the pair pu.  Class 0 holds the centre tap when
-  // the operator has one.
+  // its centre 1 + 2pu and the pair pu (degree 1) or one class per
+  // distance 0..3 (degree 3); V1 of degree 3 has {0}, {-3, 3}, {-2, 1} and
+  // {-1, 2} (P1 U1 is not symmetric).  Class 0 holds the centre tap when the
+  // operator has one.
   __host__ __device__ static constexpr int cls(int off) {
-    return OP == OP_V ? (off == 0 ? 0 : 1)
+    return OP == OP_V ? (DEG == 1 ? (off == 0 ? 0 : 1) : (off < 0 ? -off : off))
+           : OP == OP_V1 ? (DEG == 1 ? 0
+                                     : off == 0 ? 0 : (off == 3 || off == -3) ? 1 : (off == -2 || off == 1) ? 2 : 3)
            : (DEG == 3 && (OP == OP_P || OP == OP_P1)) ? ((off == 0 || off == 1) ? 0 : 1)
            : (DEG == 3 && (OP == OP_U || OP == OP_U1)) ? ((off == -1 || off == 0) ? 0 : 1)
                                                        : 0;
   }
-  static constexpr int NCLS = (OP == OP_V || (DEG == 3 && (OP == OP_P || OP == OP_P1 ||
-                                                           OP == OP_U || OP == OP_U1))) ? 2 : 1;
+  static constexpr int NCLS = OP == OP_V ? (DEG == 1 ? 2 : 4)
+                              : OP == OP_V1 ? (DEG == 1 ? 1 : 4)
+                              : (DEG == 3 && (OP == OP_P || OP == OP_P1 || OP == OP_U || OP == OP_U1)) ? 2
+                                                                                                       : 1;
   // a representative offset of each class (for its coefficient)
   __host__ __device__ static constexpr int rep(int c) {
-    return OP == OP_V ? (c == 0 ? 0 : 1)
+    return OP == OP_V ? (DEG == 1 ? (c == 0 ? 0 : 1) : c)
+           : OP == OP_V1 ? (DEG == 1 ? 0 : c == 0 ? 0 : c == 1 ? 3 : c == 2 ? 1 : 2)
            : (DEG == 3 && (OP == OP_P || OP == OP_P1)) ? (c == 0 ? 1 : 2)
            : (DEG == 3 && (OP == OP_U || OP == OP_U1)) ? (c == 0 ? -1 : 1)
                                                        : lo;
@@ -204,14 +218,37 @@ __device__ __forceinline__ float op_tap(const CS& c) {
     else return (OFF == -1 || OFF == 0) ? u1 : c.u3(K, AXIS);
   } else if constexpr (OP == OP_U0) {
     return u1;
-  } else if constexpr (OP == OP_V) {  // V = PU + 1: pu z^-1 + (1 + 2pu) + pu z
-    static_assert(DEG == 1, "V of degree 3 reaches beyond one lane");
-    // rounded products and sums (no contraction into an FMA), so that
-    // every kernel folds the same coefficient whatever its inlining context
-    return OFF == 0 ? __fadd_rn(1.0f, __fmul_rn(__fmul_rn(2.0f, p1), u1)) : __fmul_rn(p1, u1);
-  } else {  // OP_V1 = P1 U1 + 1 = 1 + pu (degree 1)
-    static_assert(DEG == 1, "V1 of degree 3 reaches beyond one lane");
-    return __fadd_rn(1.0f, __fmul_rn(p1, u1));
+  } else if constexpr (OP == OP_V) {
+    // V = PU + 1, the convolution of the taps above plus one at the centre.
+    // Rounded products and sums (no contraction into an FMA), so that every
+    // kernel folds the same coefficient whatever its inlining context.
+    if constexpr (DEG == 1) {  // pu z^-1 + (1 + 2pu) + pu z
+      return OFF == 0 ? __fadd_rn(1.0f, __fmul_rn(__fmul_rn(2.0f, p1), u1)) : __fmul_rn(p1, u1);
+    } else {  // distance 0: 1 + 2 p1 u1 + 2 p3 u3; 1: p1 u1 + p1 u3 + p3 u1; 2: p1 u3 + p3 u1; 3: p3 u3
+      const float p3 = c.p3(K, AXIS), u3 = c.u3(K, AXIS);
+      if constexpr (OFF == 0)
+        return __fadd_rn(1.0f, __fadd_rn(__fmul_rn(__fmul_rn(2.0f, p1), u1), __fmul_rn(__fmul_rn(2.0f, p3), u3)));
+      else if constexpr (OFF == 1)
+        return __fadd_rn(__fadd_rn(__fmul_rn(p1, u1), __fmul_rn(p1, u3)), __fmul_rn(p3, u1));
+      else if constexpr (OFF == 2)
+        return __fadd_rn(__fmul_rn(p1, u3), __fmul_rn(p3, u1));
+      else
+        return __fmul_rn(p3, u3);
+    }
+  } else {  // OP_V1 = P1 U1 + 1
+    if constexpr (DEG == 1) {  // 1 + pu
+      return __fadd_rn(1.0f, __fmul_rn(p1, u1));
+    } else {  // 0: 1 + p1 u1 + 2 p3 u3; +-3: p3 u3; -2, 1: p3 u1; -1, 2: p1 u3
+      const float p3 = c.p3(K, AXIS), u3 = c.u3(K, AXIS);
+      if constexpr (OFF == 0)
+        return __fadd_rn(1.0f, __fadd_rn(__fmul_rn(p1, u1), __fmul_rn(__fmul_rn(2.0f, p3), u3)));
+      else if constexpr (OFF == 3 || OFF == -3)
+        return __fmul_rn(p3, u3);
+      else if constexpr (OFF == -2 || OFF == 1)
+        return __fmul_rn(p3, u1);
+      else
+        return __fmul_rn(p1, u3);
+    }
   }
 }
 
@@ -326,16 +363,23 @@ struct Scale {
 // ---------------------------------------------------------------------------
 template <int WL, bool INV>
 struct ConvShape {
-  // [out][in] ranges of the 1-D polyphase entries (quad offsets).
+  // [out][in] ranges of the 1-D polyphase entries (quad offsets).  DD 13/7:
+  // forward L <- even 1 + UP (-3..3), L <- odd U (-2..1), H <- even P
+  // (-1..2), H <- odd 1; inverse even <- L 1, even <- H U, odd <- L P,
+  // odd <- H 1 + PU.
   __host__ __device__ static constexpr int lo(int o, int i) {
     return WL == W53 ? (!INV ? (o == 0 ? -1 : 0) : (i == 0 ? 0 : -1))
-                     : (!INV ? (o == 0 ? -2 : -1) : (i == 0 ? -1 : -2));
+           : WL == W97 ? (!INV ? (o == 0 ? -2 : -1) : (i == 0 ? -1 : -2))
+                       : (!INV ? (o == 0 ? (i == 0 ? -3 : -2) : (i == 0 ? -1 : 0))
+                               : (o == 0 ? (i == 0 ? 0 : -2) : (i == 0 ? -1 : -3)));
   }
   __host__ __device__ static constexpr int hi(int o, int i) {
     return WL == W53 ? (!INV ? (o == 0 ? (i == 0 ? 1 : 0) : (i == 0 ? 1 : 0))
                              : (o == 0 ? 0 : (i == 0 ? 1 : 1)))
-                     : (!INV ? (o == 0 ? (i == 0 ? 2 : 1) : (i == 0 ? 2 : 1))
-                             : (o == 0 ? 1 : 2));
+           : WL == W97 ? (!INV ? (o == 0 ? (i == 0 ? 2 : 1) : (i == 0 ? 2 : 1))
+                               : (o == 0 ? 1 : 2))
+                       : (!INV ? (o == 0 ? (i == 0 ? 3 : 1) : (i == 0 ? 2 : 0))
+                               : (o == 0 ? (i == 0 ? 0 : 1) : (i == 0 ? 2 : 3)));
   }
 };
 
@@ -361,7 +405,7 @@ struct Conv {
           constexpr int DY = decltype(dy)::value;
           static_for<S::lo(SX, TX), S::hi(SX, TX)>([&](auto dx) {
             constexpr int DX = decltype(dx)::value;
-            const float cf = t.t[SO][SX][TI][TX][DY + 2][DX + 2];
+            const float cf = t.t[SO][SX][TI][TX][DY + kConvReach][DX + kConvReach];
             static_for<0, QL - 1>([&](auto jj) {
               constexpr int J = decltype(jj)::value;
               sum[J] = fmaf(cf, acc.template at<2 * TI + TX, DY, DX, J>(), sum[J]);

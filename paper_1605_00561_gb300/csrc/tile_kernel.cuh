@@ -33,6 +33,14 @@ namespace dev {
 // slot per thread; PR / PC rows and columns of never-written padding around
 // each shared-memory plane absorb the reads of the outermost halo quads
 // (whose results are discarded).
+// The largest reach of one step of a program, in quads.
+template <class L>
+struct MaxStepReach;
+template <class... S>
+struct MaxStepReach<List<S...>> {
+  static constexpr int v = vmax(0, S::UP..., S::DOWN..., S::LEFT..., S::RIGHT...);
+};
+
 template <class PROG, int QL_>
 struct TileGeom {
   using Tot = Totals<PROG>;
@@ -40,7 +48,8 @@ struct TileGeom {
   static constexpr int TR = 32, TC = 32;
   static constexpr int UP = Tot::UP, DOWN = Tot::DOWN, LEFT = Tot::LEFT, RIGHT = Tot::RIGHT;
   static constexpr int IR = TR - UP - DOWN, IC = TC - LEFT - RIGHT;  // stored interior
-  static constexpr int PR = 2, PC = 4;  // a step reaches at most 2 quads; 4 keeps rows 16-byte aligned
+  // padding: a step's reach in rows, and 4 columns (rows stay 16-byte aligned)
+  static constexpr int PR = cmax(1, MaxStepReach<PROG>::v), PC = 4;
   static constexpr int RS = TC + 2 * PC;          // plane row stride (elements)
   static constexpr int PS = (TR + 2 * PR) * RS;   // plane size (elements)
   static constexpr int SLOTS_PER_ROW = TC / QL;
@@ -280,7 +289,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned* ctr, uint32_t limit, int*
 static __constant__ ConvTaps kTileNoTaps;
 
 template <class C>
-__global__ void __launch_bounds__(kTileThreads, 4) tail_kernel(const __grid_constant__ TailParams P) {
+__global__ void __launch_bounds__(kTileThreads, C::MINB) tail_kernel(const __grid_constant__ TailParams P) {
   using VT = typename C::VT;
   using G = TileGeom<typename C::PROG, C::QL>;
   constexpr int QL = G::QL;
@@ -347,7 +356,9 @@ __global__ void __launch_bounds__(kTileThreads, 4) tail_kernel(const __grid_cons
 
 // Configuration of a tail kernel: storage and arithmetic types, the step
 // program, what a level reads and writes, and the coefficient source.
-template <typename ST_, typename VT_, class PROG_, int LOAD_, int STORE_, class CSRC_>
+// MINB: resident CTAs per SM the register budget is cut for (4: 64
+// registers a thread; the merged Polyphase steps take 2, 128 registers).
+template <typename ST_, typename VT_, class PROG_, int LOAD_, int STORE_, class CSRC_, int MINB_ = 4>
 struct TailCfg {
   using ST = ST_;
   using VT = VT_;
@@ -355,6 +366,7 @@ struct TailCfg {
   using CSRC = CSRC_;
   static constexpr int LOAD = LOAD_, STORE = STORE_;
   static constexpr int QL = 4;
+  static constexpr int MINB = MINB_;
 };
 
 // Host glue of one tail kernel.

@@ -32,8 +32,7 @@ TOL_ROUND_TRIP = 2 * TOL_F32
 OID = {"cdf53": oracle.CDF53, "cdf97": oracle.CDF97, "dd137": oracle.DD137}
 FLOAT_SCHEMES = ["rowcol", "sweldens", "iwahashi", "iwahashi*", "explosive", "explosive*",
                  "monolithic", "monolithic*", "polyphase", "polyphase*", "convolution"]
-DD_SCHEMES = ["rowcol", "sweldens", "iwahashi", "iwahashi*", "explosive", "explosive*", "monolithic",
-              "monolithic*"]
+DD_SCHEMES = FLOAT_SCHEMES
 
 
 @pytest.fixture(scope="module")

@@ -22,7 +22,7 @@ TOL_F32 = 2e-3
 OID = {"cdf53": oracle.CDF53, "cdf97": oracle.CDF97, "dd137": oracle.DD137}
 TILE_SCHEMES = ["sweldens", "iwahashi", "iwahashi*", "explosive", "explosive*", "monolithic", "monolithic*",
                 "polyphase", "polyphase*"]
-DD_TILE = ["sweldens", "iwahashi", "iwahashi*", "explosive", "explosive*", "monolithic", "monolithic*"]
+DD_TILE = TILE_SCHEMES
 
 
 @pytest.fixture(scope="module")

@@ -67,10 +67,9 @@ def test_float32_forward_inverse_vs_oracle(dwt, scheme, wavelet, h, w, L):
     assert np.abs(y - x).max() <= TOL_ROUND_TRIP, "round trip"
 
 
-# DD 13/7 (degree-3 predict and update, Sec. 5): the schemes whose steps are
-# stencils of P and U themselves (Polyphase and Convolution are refused)
-DD_SCHEMES = ["rowcol", "sweldens", "iwahashi", "iwahashi*", "explosive", "explosive*", "monolithic",
-              "monolithic*"]
+# DD 13/7 (degree-3 predict and update, Sec. 5): every scheme, Polyphase(*)
+# and Convolution with the degree-6 products of P and U
+DD_SCHEMES = FLOAT_SCHEMES
 
 
 @pytest.mark.parametrize("scheme", DD_SCHEMES)
@@ -135,12 +134,13 @@ def test_zeta_normalisation_in_a_batch(dwt):
         p.close()
 
 
-def test_dd137_unsupported_combinations(dwt):
+def test_dd137_every_scheme_and_batches(dwt):
     p = dwt.dwt_plan_create(64, 64, dwt.DWT_DD137, 2, dwt.DWT_F32)
-    for name in ("polyphase", "polyphase*", "convolution"):
-        with pytest.raises(dwt.DwtError) as e:
-            dwt.dwt_plan_set_scheme(p, dwt.SCHEMES[name])
-        assert e.value.status == dwt.DWT_EUNSUPPORTED
+    for name in FLOAT_SCHEMES:
+        dwt.dwt_plan_set_scheme(p, dwt.SCHEMES[name])
+    with pytest.raises(dwt.DwtError) as e:
+        dwt.dwt_plan_create(64, 64, dwt.DWT_DD137, 2, dwt.DWT_F16S)
+    assert e.value.status == dwt.DWT_EUNSUPPORTED
     # batches run DD 13/7 plans with their Monolithic* kind
     xh = inputs.uniform_image(64, 64, seed=5)
     x = torch.from_numpy(xh).cuda()
