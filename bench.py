@@ -357,7 +357,6 @@ def time_back_to_back(torch, fn, k, warm=2):
     return e0.elapsed_time(e1) * 1e3 / k
 
 
-DD_UNSUPPORTED = ("polyphase", "polyphase*", "convolution")
 
 
 def run_sweep(a):
@@ -378,8 +377,6 @@ def run_sweep(a):
         for wl in a.wavelets.split(","):
             for L in [int(v) for v in a.sweep_levels.split(",")]:
                 for sc in schemes:
-                    if wl == "dd137" and sc in DD_UNSUPPORTED:
-                        continue
                     plan = dwt.Plan(n, n, wl, L, "f32", scheme=sc)
                     fl = flush if resident else None
                     t_f = time_calls(torch, lambda: plan.forward(x, c), a.reps, fl)

@@ -275,9 +275,18 @@ Occ occupancy(const void* fn, size_t smem, int device, int threads = kWarpsPerCt
   cudaDeviceGetAttribute(&o.sms, cudaDevAttrMultiProcessorCount, device);
   int optin = 0;
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
-  cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, optin > 0 ? optin : (int)smem);
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o.per_sm, fn, threads, smem) != cudaSuccess)
+  // the largest dynamic allocation the kernel can take: the opt-in limit
+  // less its static shared memory.  A failed call is cleared here, so that
+  // it cannot surface later as another call's error.
+  cudaFuncAttributes fa{};
+  const int stat = cudaFuncGetAttributes(&fa, fn) == cudaSuccess ? (int)fa.sharedSizeBytes : 0;
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           optin > stat ? optin - stat : (int)smem) != cudaSuccess)
+    cudaGetLastError();
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o.per_sm, fn, threads, smem) != cudaSuccess) {
+    cudaGetLastError();
     o.per_sm = 1;
+  }
   o.sms = std::max(o.sms, 1);
   o.per_sm = std::max(o.per_sm, 1);
   if (free_slot >= 0) g_occ[free_slot] = OccEntry{fn, device, smem, o};
