@@ -300,6 +300,18 @@ dwt_status dwt_plan_read_profile(dwt_plan plan, dwt_kernel_stat* stats, int capa
  * scheme and wavelet. */
 dwt_status dwt_plan_autotune(dwt_plan plan, dwt_stream stream);
 
+/* Counts of the forward program a scheme runs, computed at compile time
+ * from the same step lists as the kernels: multiply-accumulates per
+ * quadruple (every tap of every term of every step; the scaling step and
+ * the unit diagonal of a merged matrix are not operations), barriers (steps
+ * that read other quadruples: the paper's memory barriers, Sec. 5, Table of
+ * operations and barriers) and the shared-memory words per quadruple the
+ * tile kernel of the fused tail publishes before those steps.  Row-column
+ * reports its two passes together.  Host-only: needs no GPU.  Any pointer
+ * may be NULL.  Errors: DWT_EINVAL for an unknown wavelet or scheme. */
+dwt_status dwt_scheme_counts(dwt_wavelet wavelet, dwt_scheme scheme, int* macs, int* barriers,
+                             int* smem_words);
+
 dwt_status dwt_plan_destroy(dwt_plan plan);
 
 const char* dwt_status_string(dwt_status status);

@@ -21,7 +21,7 @@ __all__ = [
     "dwt2_forward", "dwt2_inverse", "dwt2_forward_noalloc", "dwt2_forward_host", "dwt2_inverse_host", "dwt_batch_submit",
     "dwt_plan_device_status", "dwt_noalloc_device_status", "dwt_set_wait_limits", "dwt_debug_inject",
     "DWT_INJECT_NONE", "DWT_INJECT_ENOMEM", "DWT_INJECT_HOLD", "DWT_INJECT_BATCH_DEP", "dwt_plan_set_profiling", "dwt_plan_read_profile", "dwt_plan_autotune",
-    "dwt_plan_destroy", "dwt_status_string", "dwt_version", "Plan", "DwtRequest",
+    "dwt_plan_destroy", "dwt_scheme_counts", "dwt_status_string", "dwt_version", "Plan", "DwtRequest",
 ]
 
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "lib", "libdwt.so")
@@ -89,6 +89,8 @@ EXPORTS = {
                                ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
     "dwt_plan_autotune": ([ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
     "dwt_plan_destroy": ([ctypes.c_void_p], ctypes.c_int),
+    "dwt_scheme_counts": ([ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                           ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
     "dwt_status_string": ([ctypes.c_int], ctypes.c_char_p),
     "dwt_version": ([], ctypes.c_char_p),
 }
@@ -228,6 +230,15 @@ def dwt_plan_read_profile(plan: int, capacity: int = 64):
 
 def dwt_plan_autotune(plan: int, stream: int = 0) -> None:
     _check(lib().dwt_plan_autotune(plan, stream), "dwt_plan_autotune")
+
+
+def dwt_scheme_counts(wavelet: int, scheme: int):
+    """(multiply-accumulates per quadruple, barriers, tile shared-memory words
+    per quadruple) of a scheme's forward program."""
+    m, b, w = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(lib().dwt_scheme_counts(wavelet, scheme, ctypes.byref(m), ctypes.byref(b), ctypes.byref(w)),
+           "dwt_scheme_counts")
+    return m.value, b.value, w.value
 
 
 def dwt_plan_destroy(plan: int) -> None:

@@ -84,3 +84,19 @@ def test_wait_limits_and_injection_arguments(libdwt):
     assert lib.dwt_debug_inject(libdwt.DWT_INJECT_ENOMEM, -1, 1) == libdwt.DWT_EINVAL
     assert lib.dwt_debug_inject(libdwt.DWT_INJECT_ENOMEM, 0, -1) == libdwt.DWT_EINVAL
     assert lib.dwt_debug_inject(libdwt.DWT_INJECT_NONE, 0, 0) == libdwt.DWT_OK
+
+
+def test_scheme_counts_reproduce_the_papers_table(libdwt, golden):
+    """Multiply-accumulates per quadruple and barriers of the programs the
+    kernels run (counted at compile time from their step lists) against the
+    paper's Table of operations and barriers (Sec. 5): all 30 rows."""
+    wl = {"CDF 5/3": libdwt.DWT_CDF53, "CDF 9/7": libdwt.DWT_CDF97, "DD 13/7": libdwt.DWT_DD137}
+    rows = golden("op_barrier_counts.txt")
+    assert len(rows) == 30
+    for wavelet, scheme, barriers, ops in rows:
+        name = scheme.lower()
+        m, b, w = libdwt.dwt_scheme_counts(wl[wavelet], libdwt.SCHEMES[name])
+        assert (m, b) == (int(ops), int(barriers)), (wavelet, scheme, m, b)
+        assert w >= b  # each barrier step publishes at least one subband
+    with pytest.raises(libdwt.DwtError):
+        libdwt.dwt_scheme_counts(7, libdwt.SCHEMES["sweldens"])
