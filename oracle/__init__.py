@@ -20,7 +20,7 @@ import numpy as np
 __all__ = [
     "CDF53", "CDF97", "DD137", "NORM_JPEG2000", "NORM_ZETA", "build", "lib",
     "mirror", "cdf97_constants", "lifting", "dwt1", "dwt1_int", "dwt2",
-    "dwt2_int", "max_levels", "OracleRangeError",
+    "dwt2_int", "dwt2_int_iwahashi", "max_levels", "OracleRangeError",
 ]
 
 CDF53, CDF97, DD137 = 0, 1, 2
@@ -69,6 +69,8 @@ def lib() -> ctypes.CDLL:
         l.oracle_dwt2_f64.restype = ctypes.c_int
         l.oracle_dwt2_i64.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ip, ip]
         l.oracle_dwt2_i64.restype = ctypes.c_int
+        l.oracle_dwt2_iwahashi_i64.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ip, ip]
+        l.oracle_dwt2_iwahashi_i64.restype = ctypes.c_int
         l.oracle_max_levels.argtypes = [ctypes.c_int, ctypes.c_int]
         l.oracle_max_levels.restype = ctypes.c_int
         _lib = l
@@ -145,6 +147,21 @@ def dwt2_int(x, levels: int, inverse: bool = False) -> np.ndarray:
     h, w = a.shape
     out = np.empty_like(a)
     rc = lib().oracle_dwt2_i64(int(inverse), w, h, levels, _iptr(a), _iptr(out))
+    if rc == -2:
+        raise OracleRangeError("an intermediate left the int32 range")
+    if rc != 0:
+        raise ValueError(f"invalid arguments (rc={rc})")
+    return out
+
+
+def dwt2_int_iwahashi(x, levels: int, inverse: bool = False) -> np.ndarray:
+    """L-level reversible integer non-separable lifting (the Iwahashi scheme
+    of CDF 5/3 with each step's update rounded once), exact int64 with an
+    int32 range check; see dwt_oracle.h for the definition."""
+    a = np.ascontiguousarray(x, dtype=np.int64)
+    h, w = a.shape
+    out = np.empty_like(a)
+    rc = lib().oracle_dwt2_iwahashi_i64(int(inverse), w, h, levels, _iptr(a), _iptr(out))
     if rc == -2:
         raise OracleRangeError("an intermediate left the int32 range")
     if rc != 0:

@@ -359,3 +359,106 @@ int oracle_dwt2_i64(int inverse, int w, int h, int levels, const int64_t* in,
   }
   return g_range_error ? -2 : 0;
 }
+
+/* ------------------------------------------------------------------ */
+/* Reversible integer non-separable lifting (Iwahashi scheme, CDF 5/3)  */
+/* ------------------------------------------------------------------ */
+
+/* Sample (r, c) of a w x h plane with whole-sample symmetric extension; on
+ * an axis of length 1 the samples of odd parity do not exist and read 0. */
+static int64_t iw_get(const int64_t* t, long w, long h, long r, long c) {
+  if ((w == 1 && c != 0) || (h == 1 && r != 0)) return 0;
+  return t[oracle_mirror(r, h) * w + oracle_mirror(c, w)];
+}
+
+/* Neighbour sums of sample (r, c): horizontal (left + right), vertical
+ * (above + below) and diagonal (the four corners). */
+static int64_t iw_h(const int64_t* t, long w, long h, long r, long c) {
+  return iw_get(t, w, h, r, c - 1) + iw_get(t, w, h, r, c + 1);
+}
+static int64_t iw_v(const int64_t* t, long w, long h, long r, long c) {
+  return iw_get(t, w, h, r - 1, c) + iw_get(t, w, h, r + 1, c);
+}
+static int64_t iw_d(const int64_t* t, long w, long h, long r, long c) {
+  return iw_get(t, w, h, r - 1, c - 1) + iw_get(t, w, h, r - 1, c + 1) + iw_get(t, w, h, r + 1, c - 1) +
+         iw_get(t, w, h, r + 1, c + 1);
+}
+
+/* The rounded update of one sample in step `step` (0: T, 1: R, 2: S), read
+ * from the current plane: the Iwahashi step matrices (Sec. 2.6) with
+ * p = -1/2 and u = 1/4, each step's whole update rounded once (half up). */
+static int64_t iw_delta(int step, const int64_t* t, long w, long h, long r, long c) {
+  const int ro = (int)(r & 1), co = (int)(c & 1);
+  if (step == 0) /* T^I_P: HH += p h(LH) + p v(HL) + p^2 d(LL) */
+    return floor_div(chk(iw_d(t, w, h, r, c) - 2 * (iw_h(t, w, h, r, c) + iw_v(t, w, h, r, c)) + 2), 4);
+  if (step == 1) {
+    if (!ro && co) /* R^I, HL += p h(LL) + u v(HH) */
+      return floor_div(chk(iw_v(t, w, h, r, c) - 2 * iw_h(t, w, h, r, c) + 2), 4);
+    /* R^I, LH += p v(LL) + u h(HH) */
+    return floor_div(chk(iw_h(t, w, h, r, c) - 2 * iw_v(t, w, h, r, c) + 2), 4);
+  }
+  /* S^I_U: LL += u h(HL) + u v(LH) - u^2 d(HH) */
+  return floor_div(chk(4 * (iw_h(t, w, h, r, c) + iw_v(t, w, h, r, c)) - iw_d(t, w, h, r, c) + 8), 16);
+}
+
+/* Whether sample (r, c) is a target of step `step`: T writes HH (odd,
+ * odd), R writes HL (even, odd) and LH (odd, even), S writes LL. */
+static int iw_target(int step, long r, long c) {
+  const int ro = (int)(r & 1), co = (int)(c & 1);
+  if (step == 0) return ro && co;
+  if (step == 1) return ro != co;
+  return !ro && !co;
+}
+
+/* One step on the whole plane: every update is computed from the pre-step
+ * plane (a step's targets are not among its sources), then applied. */
+static int iw_step(int step, int sign, int64_t* t, long w, long h) {
+  int64_t* dlt = (int64_t*)malloc(sizeof(int64_t) * (size_t)w * (size_t)h);
+  if (!dlt) return -1;
+  for (long r = 0; r < h; ++r)
+    for (long c = 0; c < w; ++c)
+      dlt[r * w + c] = iw_target(step, r, c) ? iw_delta(step, t, w, h, r, c) : 0;
+  for (long i = 0; i < w * h; ++i) t[i] = chk(t[i] + sign * dlt[i]);
+  free(dlt);
+  return 0;
+}
+
+int oracle_dwt2_iwahashi_i64(int inverse, int w, int h, int levels, const int64_t* in, int64_t* out) {
+  if (check_args(w, h, levels) != 0) return -1;
+  if (out != in) memcpy(out, in, sizeof(int64_t) * (size_t)w * (size_t)h);
+  g_range_error = 0;
+  for (size_t i = 0; i < (size_t)w * (size_t)h; ++i) chk(out[i]);
+  int wk[64], hk[64];
+  wk[0] = w;
+  hk[0] = h;
+  for (int k = 1; k <= levels; ++k) {
+    wk[k] = (wk[k - 1] + 1) / 2;
+    hk[k] = (hk[k - 1] + 1) / 2;
+  }
+  int64_t* t = (int64_t*)malloc(sizeof(int64_t) * (size_t)w * (size_t)h);
+  if (!t) return -1;
+  for (int s = 0; s < levels; ++s) {
+    const int k = inverse ? levels - 1 - s : s;
+    const long W = wk[k], H = hk[k], cw = (W + 1) / 2, ch = (H + 1) / 2;
+    if (!inverse) {
+      for (long r = 0; r < H; ++r)
+        for (long c = 0; c < W; ++c) t[r * W + c] = out[r * (size_t)w + c];
+      for (int step = 0; step < 3; ++step)
+        if (iw_step(step, 1, t, W, H)) return -1;
+      /* Mallat packing: even rows / columns to the low halves */
+      for (long r = 0; r < H; ++r)
+        for (long c = 0; c < W; ++c)
+          out[((r & 1) ? ch + r / 2 : r / 2) * (size_t)w + ((c & 1) ? cw + c / 2 : c / 2)] = t[r * W + c];
+    } else {
+      for (long r = 0; r < H; ++r)
+        for (long c = 0; c < W; ++c)
+          t[r * W + c] = out[((r & 1) ? ch + r / 2 : r / 2) * (size_t)w + ((c & 1) ? cw + c / 2 : c / 2)];
+      for (int step = 2; step >= 0; --step)
+        if (iw_step(step, -1, t, W, H)) return -1;
+      for (long r = 0; r < H; ++r)
+        for (long c = 0; c < W; ++c) out[r * (size_t)w + c] = t[r * W + c];
+    }
+  }
+  free(t);
+  return g_range_error ? -2 : 0;
+}

@@ -73,6 +73,20 @@ int oracle_dwt2_f64(int wavelet, int norm, int inverse, int w, int h,
 int oracle_dwt2_i64(int inverse, int w, int h, int levels, const int64_t* in,
                     int64_t* out);
 
+/* Reversible integer non-separable lifting: the Iwahashi scheme (Sec. 2.6)
+ * of CDF 5/3 (p = -1/2, u = 1/4) with each step's whole update rounded once,
+ * half up -- a different reversible transform from the JPEG 2000 one above
+ * (whose every 1-D step rounds on its own).  In sample coordinates, with
+ * h, v, d the horizontal, vertical and diagonal neighbour sums (whole-sample
+ * symmetric extension; absent samples of a length-1 axis read 0):
+ *   T: odd row, odd col    += floor((d - 2 (h + v) + 2) / 4)
+ *   R: even row, odd col   += floor((v - 2 h + 2) / 4)
+ *      odd row, even col   += floor((h - 2 v + 2) / 4)
+ *   S: even row, even col  += floor((4 (h + v) - d + 8) / 16)
+ * Each step reads only samples it does not write, so the inverse subtracts
+ * the same updates in the order S, R, T.  Mallat packing as above. */
+int oracle_dwt2_iwahashi_i64(int inverse, int w, int h, int levels, const int64_t* in, int64_t* out);
+
 /* Largest valid level count: halvings until both dimensions are 1. */
 int oracle_max_levels(int w, int h);
 

@@ -418,3 +418,56 @@ def test_max_levels_and_invalid_arguments():
         oracle.dwt2(np.zeros((4, 4)), oracle.CDF53, 3)
     with pytest.raises(ValueError):
         oracle.dwt2(np.zeros((4, 4)), oracle.CDF53, -1)
+
+
+# ----------------------------------------------------------------------------
+# reversible integer non-separable lifting (the integer Iwahashi scheme)
+# ----------------------------------------------------------------------------
+
+def test_integer_iwahashi_golden(golden):
+    rows = golden("int_iwahashi_vectors.txt")
+    assert len(rows) == 2
+    for name, h, w, L, x, y in rows:
+        h, w, L = int(h), int(w), int(L)
+        x = np.array(_ints(x)).reshape(h, w)
+        want = np.array(_ints(y)).reshape(h, w)
+        got = oracle.dwt2_int_iwahashi(x, L)
+        assert np.array_equal(got, want), name
+        assert np.array_equal(oracle.dwt2_int_iwahashi(got, L, inverse=True), x), name
+
+
+@pytest.mark.parametrize("h,w,L", [(33, 47, 5), (64, 64, 6), (5, 2, 3), (1, 13, 4), (13, 1, 4), (2, 2, 1)])
+def test_integer_iwahashi_exact_round_trip(h, w, L):
+    x = np.random.default_rng(h * 11 + w).integers(0, 4096, (h, w))
+    y = oracle.dwt2_int_iwahashi(x, L)
+    assert np.array_equal(oracle.dwt2_int_iwahashi(y, L, inverse=True), x)
+    # a different reversible transform from the JPEG 2000 one
+    if h > 2 and w > 2:
+        assert not np.array_equal(y, oracle.dwt2_int(x, L))
+
+
+def test_integer_iwahashi_linear_ramps_and_constants():
+    r, c = np.mgrid[0:20, 0:22]
+    y = oracle.dwt2_int_iwahashi(3 * c + 7 * r + 11, 1)
+    # the predict of a linear ramp is exact away from the borders
+    assert np.all(y[2:8, 13:19] == 0) and np.all(y[12:18, 2:9] == 0) and np.all(y[12:18, 13:19] == 0)
+    yc = oracle.dwt2_int_iwahashi(np.full((20, 22), 1234), 3)
+    assert np.all(yc[:3, :3] == 1234) and np.count_nonzero(yc) == 9
+
+
+def test_integer_iwahashi_error_intervals_against_float():
+    # Each step rounds its whole update once, half up: an error in (-1/2,
+    # 1/2] per step.  T leaves HH within 1/2 of the float transform; R adds
+    # u (two HH errors) to its own, so HL, LH within 3/4; S adds u (four
+    # HL/LH errors, 3/4 in all) and u^2 (four HH errors, 1/8 in all) to its
+    # own, so LL within 11/8.  Without the rounding offsets the intervals
+    # shift by 1/2 and random images leave them.
+    rng = np.random.default_rng(23)
+    for h, w in ((40, 36), (33, 47), (2, 9), (64, 64), (9, 2)):
+        x = rng.integers(0, 4096, (h, w))
+        e = oracle.dwt2_int_iwahashi(x, 1) - oracle.dwt2(x.astype(float), oracle.CDF53, 1)
+        ch, cw = (h + 1) // 2, (w + 1) // 2
+        assert np.abs(e[ch:, cw:]).max() <= 0.5
+        assert np.abs(e[:ch, cw:]).max() <= 0.75 and np.abs(e[ch:, :cw]).max() <= 0.75
+        assert np.abs(e[:ch, :cw]).max() <= 11 / 8
+        assert np.abs(e).max() > 0
