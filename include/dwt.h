@@ -106,9 +106,18 @@ dwt_status dwt_plan_create(int w, int h, dwt_wavelet wavelet, int levels, dwt_dt
                            dwt_plan* out);
 
 /* Select the lifting scheme (default DWT_AUTO).  DWT_I32 supports
- * DWT_ROWCOL and DWT_SWELDENS (the JPEG 2000 step order with floors is not
- * shared by the non-separable schemes): other schemes give
- * DWT_EUNSUPPORTED.  DWT_ROWCOL allocates a w x h intermediate plane. */
+ * DWT_ROWCOL and DWT_SWELDENS, which compute the JPEG 2000 reversible 5/3
+ * (its step order with floors is not shared by the non-separable schemes),
+ * and DWT_IWAHASHI, which selects a different reversible transform: the
+ * non-separable Iwahashi scheme (Sec. 2.6) with each 2-D step's whole
+ * update rounded once, half up (T: HH += (d(LL) - 2 (h(LH) + v(HL)) + 2)
+ * >> 2; R: HL += (v(HH) - 2 h(LL) + 2) >> 2, LH += (h(HH) - 2 v(LL) + 2) >>
+ * 2; S: LL += (4 (h(HL) + v(LH)) - d(HH) + 8) >> 4; the inverse subtracts
+ * the same updates in the order S, R, T), exactly reversible but not
+ * JPEG 2000 compatible.  DWT_AUTO and the autotuner never switch an int32
+ * plan to it, and batches refuse it (DWT_EUNSUPPORTED).  Other schemes give
+ * DWT_EUNSUPPORTED for DWT_I32.  DWT_ROWCOL allocates a w x h intermediate
+ * plane. */
 dwt_status dwt_plan_set_scheme(dwt_plan plan, dwt_scheme scheme);
 
 /* Tile shape of the kernels (autotuner knobs).  strip_rows: target number

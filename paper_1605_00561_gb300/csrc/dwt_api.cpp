@@ -610,10 +610,21 @@ int default_scheme(const dwt_plan_s* p) {
 
 bool scheme_supported(int wavelet, int dtype, int scheme) {
   if (scheme <= DWT_AUTO || scheme >= NUM_SCHEMES) return false;
-  if (dtype == DWT_I32) return wavelet == DWT_CDF53 && (scheme == DWT_ROWCOL || scheme == DWT_SWELDENS);
+  // int32: the JPEG 2000 reversible 5/3 (row-column or single-loop), or the
+  // reversible integer Iwahashi lifting, a transform of its own
+  if (dtype == DWT_I32)
+    return wavelet == DWT_CDF53 && (scheme == DWT_ROWCOL || scheme == DWT_SWELDENS || scheme == DWT_IWAHASHI);
   // DD 13/7 (degree-3 pairs): float32, every scheme
   if (wavelet == DWT_DD137) return dtype == DWT_F32;
   return true;
+}
+
+// Schemes the autotuner may choose among: every scheme of the plan's
+// wavelet and storage type, except that int32 stays with the JPEG 2000
+// transform (the integer Iwahashi lifting gives other coefficients and is
+// only run when a caller selects it).
+bool tunable(int wavelet, int dtype, int scheme) {
+  return scheme_supported(wavelet, dtype, scheme) && !(dtype == DWT_I32 && scheme == DWT_IWAHASHI);
 }
 
 // Applies a cached autotuner choice once per plan: the scheme when the
@@ -623,7 +634,7 @@ void apply_cache(dwt_plan_s* p) {
   p->tuned = true;
   const Tuned t = cache_lookup(cache_key(p));
   if (p->auto_scheme < 0)
-    p->auto_scheme = scheme_supported(p->wavelet, p->dtype, t.scheme) ? t.scheme : default_scheme(p);
+    p->auto_scheme = tunable(p->wavelet, p->dtype, t.scheme) ? t.scheme : default_scheme(p);
   if (!p->tile_set && t.rows > 0 && t.stages >= 1 && t.stages <= kMaxStages) {
     p->strip_rows = t.rows;
     p->nstages = t.stages;
@@ -1193,6 +1204,8 @@ dwt_status batch_submit(const dwt_request* reqs, int n, cudaStream_t s, int* d_s
     if (chk != DWT_OK) return chk;
     kinds[i] = batch_kind(p->wavelet, p->dtype, reqs[i].inverse != 0);
     if (kinds[i] < 0) return DWT_EUNSUPPORTED;
+    // the batch's int32 kind is the JPEG 2000 transform
+    if (p->dtype == DWT_I32 && p->scheme == DWT_IWAHASHI) return DWT_EUNSUPPORTED;
     with_dd = with_dd || p->wavelet == DWT_DD137;
     maxl = std::max(maxl, p->levels);
   }
@@ -1829,7 +1842,10 @@ dwt_status dwt_plan_autotune(dwt_plan p, dwt_stream stream) {
   p->strip_rows = 0;
   p->nstages = kDefaultStages;
   for (int sc = DWT_ROWCOL; e == cudaSuccess && sc < NUM_SCHEMES; ++sc) {
-    if (!scheme_supported(p->wavelet, p->dtype, sc)) continue;
+    // an int32 plan set to the integer Iwahashi lifting keeps that
+    // transform (only its tile is tuned); others choose among the rest
+    const bool iw_int = p->dtype == DWT_I32 && saved_scheme == DWT_IWAHASHI;
+    if (iw_int ? sc != DWT_IWAHASHI : !tunable(p->wavelet, p->dtype, sc)) continue;
     p->scheme = sc;
     if (sc == DWT_ROWCOL && ensure_tmp(p) != DWT_OK) continue;
     float t;

@@ -195,6 +195,12 @@ struct IntFused {
       !INV, List<Int53<0, false>, Int53<1, false>, Int53<2, false>, Int53<3, false>>,
       List<Int53<3, true>, Int53<2, true>, Int53<1, true>, Int53<0, true>>>::type;
 };
+// Reversible integer Iwahashi lifting (its own rounding): T, R, S.
+template <bool INV>
+struct IntIwFused {
+  using type = typename std::conditional<!INV, List<IntIw<0, false>, IntIw<1, false>, IntIw<2, false>>,
+                                         List<IntIw<2, true>, IntIw<1, true>, IntIw<0, true>>>::type;
+};
 template <int PASS, bool INV>
 struct IntPass {
   using type = typename std::conditional<

@@ -479,6 +479,74 @@ struct Int53 {
 };
 
 // ---------------------------------------------------------------------------
+// Reversible integer non-separable lifting: the Iwahashi scheme (Sec. 2.6)
+// of CDF 5/3 (p = -1/2, u = 1/4) with each step's whole update rounded once,
+// half up -- a different reversible transform from the JPEG 2000 one, whose
+// 1-D steps round one by one.  Every step reads only subbands it does not
+// write, so the inverse subtracts the same updates in reverse order.  On an
+// axis of length 1 the absent subbands stay 0: their updates are skipped.
+//   KIND 0, T^I_P: HH += (d(LL) - 2 (h(LH) + v(HL)) + 2) >> 2
+//   KIND 1, R^I:   HL += (v(HH) - 2 h(LL) + 2) >> 2,  LH += (h(HH) - 2 v(LL) + 2) >> 2
+//   KIND 2, S^I_U: LL += (4 (h(HL) + v(LH)) - d(HH) + 8) >> 4
+// with h, v, d the horizontal, vertical and diagonal neighbour sums in
+// quad offsets of the JPEG 2000 origin (predicts read {0, +1}, updates
+// {-1, 0}).
+// ---------------------------------------------------------------------------
+template <int KIND, bool INV>
+struct IntIw {
+  static constexpr int UP = KIND == 0 ? 0 : 1;
+  static constexpr int DOWN = KIND == 2 ? 0 : 1;
+  static constexpr int LEFT = KIND == 0 ? 0 : 1;
+  static constexpr int RIGHT = KIND == 2 ? 0 : 1;
+  static constexpr unsigned NEIGHBOUR_SRCS = KIND == 0   ? (1u << LL) | (1u << HL) | (1u << LH)
+                                             : KIND == 1 ? (1u << LL) | (1u << HH)
+                                                         : (1u << HL) | (1u << LH) | (1u << HH);
+
+  template <int QL, class A, class CS>
+  __device__ __forceinline__ static void eval(const Row<int, QL>& own, const A& acc, Row<int, QL>& o,
+                                              const CS& c, const ConvTaps&) {
+    o = own;
+    const int sg = INV ? -1 : 1;
+    if constexpr (KIND == 0) {
+      if (c.h_on() && c.v_on()) {
+        static_for<0, QL - 1>([&](auto jj) {
+          constexpr int J = decltype(jj)::value;
+          const int d = acc.template at<LL, 0, 0, J>() + acc.template at<LL, 0, 1, J>() +
+                        acc.template at<LL, 1, 0, J>() + acc.template at<LL, 1, 1, J>();
+          const int hv = acc.template at<LH, 0, 0, J>() + acc.template at<LH, 0, 1, J>() +
+                         acc.template at<HL, 0, 0, J>() + acc.template at<HL, 1, 0, J>();
+          o.s[HH][J] += sg * ((d - 2 * hv + 2) >> 2);
+        });
+      }
+    } else if constexpr (KIND == 1) {
+      const bool hon = c.h_on(), von = c.v_on();
+      static_for<0, QL - 1>([&](auto jj) {
+        constexpr int J = decltype(jj)::value;
+        if (hon) {
+          const int v = acc.template at<HH, -1, 0, J>() + acc.template at<HH, 0, 0, J>();
+          const int hl = acc.template at<LL, 0, 0, J>() + acc.template at<LL, 0, 1, J>();
+          o.s[HL][J] += sg * ((v - 2 * hl + 2) >> 2);
+        }
+        if (von) {
+          const int h = acc.template at<HH, 0, -1, J>() + acc.template at<HH, 0, 0, J>();
+          const int vl = acc.template at<LL, 0, 0, J>() + acc.template at<LL, 1, 0, J>();
+          o.s[LH][J] += sg * ((h - 2 * vl + 2) >> 2);
+        }
+      });
+    } else {
+      static_for<0, QL - 1>([&](auto jj) {
+        constexpr int J = decltype(jj)::value;
+        const int hv = acc.template at<HL, 0, -1, J>() + acc.template at<HL, 0, 0, J>() +
+                       acc.template at<LH, -1, 0, J>() + acc.template at<LH, 0, 0, J>();
+        const int d = acc.template at<HH, -1, -1, J>() + acc.template at<HH, -1, 0, J>() +
+                      acc.template at<HH, 0, -1, J>() + acc.template at<HH, 0, 0, J>();
+        o.s[LL][J] += sg * ((4 * hv - d + 8) >> 4);
+      });
+    }
+  }
+};
+
+// ---------------------------------------------------------------------------
 // Type lists and the streaming pipeline
 // ---------------------------------------------------------------------------
 template <class... S>
