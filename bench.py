@@ -412,7 +412,10 @@ def run_sweep(a):
         c = torch.empty_like(x)
         y = torch.empty_like(x)
         for L in (1, 5):
-            for sc in ("rowcol", "sweldens"):
+            # rowcol and sweldens: the JPEG 2000 reversible 5/3; iwahashi:
+            # the reversible integer Iwahashi lifting (a transform of its own,
+            # reported under its own wavelet name)
+            for sc in ("rowcol", "sweldens", "iwahashi"):
                 if sc not in schemes:
                     continue
                 plan = dwt.Plan(w, h, "cdf53", L, "i32", scheme=sc)
@@ -424,10 +427,12 @@ def run_sweep(a):
                 plan.close()
                 ab = sum(2 * 4 * a_ * b_ for a_, b_ in level_sizes(w, h, L))
                 for d, t in (("fwd", t_f), ("inv", t_i)):
-                    rows.append({"size": f"{w}x{h}", "wavelet": "int53", "levels": L, "dir": d, "scheme": sc,
+                    rows.append({"size": f"{w}x{h}", "wavelet": "int-iwahashi" if sc == "iwahashi" else "int53",
+                                 "levels": L, "dir": d, "scheme": sc,
                                  "us": t, "gpx_s": w * h / t / 1e3, "hbm_frac": ab / (t * 1e-6) / 1e9 / peak,
                                  "l2": "larger than L2"})
             tuned[(f"{w}x{h}", "int53", L)] = ("-", (0, 0))
+            tuned[(f"{w}x{h}", "int-iwahashi", L)] = ("-", (0, 0))
         del x, c, y
         torch.cuda.empty_cache()
     best = {}
