@@ -70,7 +70,8 @@ def parse():
     ap.add_argument("--batch-lo", type=int, default=256)
     ap.add_argument("--batch-hi", type=int, default=4096)
     ap.add_argument("--batch-levels", type=int, default=3)
-    ap.add_argument("--rate", type=float, default=2000.0, help="serving: mean arrivals per second")
+    ap.add_argument("--rates", default="2000,8000",
+                    help="serving: comma-separated mean arrival rates (requests per second)")
     ap.add_argument("--seconds", type=float, default=20.0, help="serving: length of the arrival stream")
     ap.add_argument("--saturate", type=int, default=2000, help="serving: requests in the saturation run")
     return ap.parse_args()
@@ -648,8 +649,11 @@ def run_serving(a):
                                         "f32" if f else "i32", False, src))
         return reqs
 
-    trace = inputs.serving_trace(rate=a.rate, seconds=a.seconds, seed=9)
-    out = {"mode": "serving", "rate_req_s": a.rate, "seconds": a.seconds, "requests": len(trace),
+    rates = [float(r) for r in a.rates.split(",")]
+    traces = {r: inputs.serving_trace(rate=r, seconds=a.seconds, seed=9) for r in rates}
+    trace = traces[rates[0]]
+    out = {"mode": "serving", "rates_req_s": rates, "seconds": a.seconds,
+           "requests": {str(r): len(t) for r, t in traces.items()},
            "workload": "Poisson arrivals, area log-normal (median 1 MP, sigma 1), aspect U(0.5, 2), "
                        "sides clipped to [64, 8192], levels U{1..6}, 70% CDF 9/7 float32 / 30% int 5/3; "
                        "inputs are views of a device-resident pool (no host copies)"}
@@ -665,12 +669,14 @@ def run_serving(a):
         srv = server(per)
         serving.replay(srv, warm, [0.0] * len(warm))
         srv.close()
-    for name, per in (("batched", False), ("one_launch_per_request", True)):
-        srv = server(per)
-        res = serving.replay(srv, build(trace), [t["t"] for t in trace])
-        out[name] = res.summary()
-        srv.close()
-        torch.cuda.empty_cache()
+    for r in rates:
+        tr = traces[r]
+        for name, per in (("batched", False), ("one_launch_per_request", True)):
+            srv = server(per)
+            res = serving.replay(srv, build(tr), [t["t"] for t in tr])
+            out[f"{name}@{r:g}"] = res.summary()
+            srv.close()
+            torch.cuda.empty_cache()
     sat = trace[: a.saturate]
     for name, per in (("batched", False), ("one_launch_per_request", True)):
         srv = server(per)
