@@ -50,12 +50,17 @@ constexpr int kMinWarps =
 template <int SCHEME>
 constexpr bool kHasDegree3 = true;
 
+// Convolution with compile-time taps needs no tap table in registers
+// (112-127 registers against 255 with the runtime table): 16 warps per SM.
+template <int SCHEME, int WL, bool STATIC>
+constexpr int kMinWarpsCfg = (SCHEME == CONVOLUTION && STATIC) ? 16 : kMinWarps<SCHEME, WL>;
+
 // STATIC: coefficients folded in at compile time (StCoefs), for levels with
 // JPEG 2000 normalisation and both axes longer than one sample.
 template <int SCHEME, int WL, typename ST, bool INV, bool STATIC = false>
 using FusedCfg = Cfg<ST, float, typename FusedProgram<SCHEME, WL, INV>::type, INV ? SUBBANDS : SAMPLES,
                      INV ? SAMPLES : SUBBANDS, kQuadsPerLane<SCHEME, WL>, 8 / kQuadsPerLane<SCHEME, WL>,
-                     kMinWarps<SCHEME, WL>, std::conditional_t<STATIC, StCoefs<WL, INV>, RtTag>>;
+                     kMinWarpsCfg<SCHEME, WL, STATIC>, std::conditional_t<STATIC, StCoefs<WL, INV>, RtTag>>;
 
 template <int SCHEME, int WL, typename ST, bool STATIC>
 inline bool fused_dir(bool inv, int ns, KernelInfo* info, const LaunchCall* call, cudaError_t* err) {

@@ -6,7 +6,7 @@ namespace dwt {
 
 bool group_convolution(const LaunchKey& k, int ns, KernelInfo* info, const LaunchCall* call,
                    cudaError_t* err) {
-  if (dev::fused_float<CONVOLUTION>(k, ns, info, call, err)) return true;
+  if (dev::fused_float<CONVOLUTION, true>(k, ns, info, call, err)) return true;
   return false;
 }
 

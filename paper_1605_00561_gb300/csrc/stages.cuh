@@ -383,6 +383,86 @@ struct ConvShape {
   }
 };
 
+// The 1-D polyphase matrix of the whole factorisation (rows: outputs,
+// columns: inputs, Laurent polynomials in the quad offset -4..4), computed
+// at compile time from the lifting constants with JPEG 2000 normalisation:
+// forward (L, H) <- (even, odd), H += P L and L += U H per pair, then the
+// band gains; inverse (even, odd) <- (L, H), the steps undone in reverse
+// order.  The same arithmetic in the same order as the host's tap table
+// for the runtime path.
+struct ConvPoly {
+  double c[9];
+};
+struct ConvMat {
+  ConvPoly m[2][2];
+};
+__host__ __device__ constexpr ConvPoly conv_pmul(const ConvPoly& a, const ConvPoly& b) {
+  ConvPoly r{};
+  for (int i = 0; i < 9; ++i)
+    for (int j = 0; j < 9; ++j) {
+      const int k = i + j - 4;
+      if (a.c[i] != 0 && b.c[j] != 0 && k >= 0 && k < 9) r.c[k] += a.c[i] * b.c[j];
+    }
+  return r;
+}
+__host__ __device__ constexpr void conv_padd(ConvPoly& a, const ConvPoly& b, double s) {
+  for (int i = 0; i < 9; ++i) a.c[i] += s * b.c[i];
+}
+template <int WL, bool INV>
+__host__ __device__ constexpr ConvMat conv_matrix() {
+  const int npairs = WL == W97 ? 2 : 1;
+  const double p1[2] = {WL == W97 ? kAlpha : WL == W53 ? -0.5 : -9.0 / 16.0, kGamma};
+  const double u1[2] = {WL == W97 ? kBeta : WL == W53 ? 0.25 : 9.0 / 32.0, kDelta};
+  const double p3 = WL == WDD ? 1.0 / 16.0 : 0.0, u3 = WL == WDD ? -1.0 / 32.0 : 0.0;
+  const double dc = WL == W97 ? kK97 : 1.0;
+  const double lo = 1.0 / dc, hi = dc;
+  ConvMat r{};
+  if (!INV) {
+    r.m[0][0].c[4] = r.m[1][1].c[4] = 1.0;
+    for (int k = 0; k < npairs; ++k) {
+      ConvPoly P{}, U{};
+      P.c[4] = P.c[5] = p1[k];
+      P.c[3] = P.c[6] = k == 0 ? p3 : 0.0;
+      U.c[3] = U.c[4] = u1[k];
+      U.c[2] = U.c[5] = k == 0 ? u3 : 0.0;
+      for (int j = 0; j < 2; ++j) conv_padd(r.m[1][j], conv_pmul(P, r.m[0][j]), 1.0);
+      for (int j = 0; j < 2; ++j) conv_padd(r.m[0][j], conv_pmul(U, r.m[1][j]), 1.0);
+    }
+    for (int j = 0; j < 2; ++j)
+      for (int i = 0; i < 9; ++i) {
+        r.m[0][j].c[i] *= lo;
+        r.m[1][j].c[i] *= hi;
+      }
+  } else {
+    r.m[0][0].c[4] = 1.0 / lo;
+    r.m[1][1].c[4] = 1.0 / hi;
+    for (int k = npairs - 1; k >= 0; --k) {
+      ConvPoly P{}, U{};
+      P.c[4] = P.c[5] = p1[k];
+      P.c[3] = P.c[6] = k == 0 ? p3 : 0.0;
+      U.c[3] = U.c[4] = u1[k];
+      U.c[2] = U.c[5] = k == 0 ? u3 : 0.0;
+      for (int j = 0; j < 2; ++j) conv_padd(r.m[0][j], conv_pmul(U, r.m[1][j]), -1.0);
+      for (int j = 0; j < 2; ++j) conv_padd(r.m[1][j], conv_pmul(P, r.m[0][j]), -1.0);
+    }
+  }
+  return r;
+}
+template <int WL, bool INV>
+struct ConvStatic {
+  static constexpr ConvMat M = conv_matrix<WL, INV>();
+  // tap of output (SO, SX) from input (TI, TX) at quad offset (DY, DX)
+  template <int SO, int SX, int TI, int TX, int DY, int DX>
+  __device__ __forceinline__ static constexpr float tap() {
+    return float(M.m[SO][TI].c[DY + 4] * M.m[SX][TX].c[DX + 4]);
+  }
+};
+
+template <class CS>
+struct IsStaticCoefs : std::false_type {};
+template <int WL, bool INV>
+struct IsStaticCoefs<StCoefs<WL, INV>> : std::true_type {};
+
 template <int WL, bool INV>
 struct Conv {
   using S = ConvShape<WL, INV>;
@@ -405,7 +485,15 @@ struct Conv {
           constexpr int DY = decltype(dy)::value;
           static_for<S::lo(SX, TX), S::hi(SX, TX)>([&](auto dx) {
             constexpr int DX = decltype(dx)::value;
-            const float cf = t.t[SO][SX][TI][TX][DY + kConvReach][DX + kConvReach];
+            // compile-time taps for levels with static coefficients
+            // (JPEG 2000 normalisation, both sides >= 2), else the table
+            float cf;
+            if constexpr (IsStaticCoefs<CS>::value) {
+              constexpr float k = ConvStatic<WL, INV>::template tap<SO, SX, TI, TX, DY, DX>();
+              cf = k;
+            } else {
+              cf = t.t[SO][SX][TI][TX][DY + kConvReach][DX + kConvReach];
+            }
             static_for<0, QL - 1>([&](auto jj) {
               constexpr int J = decltype(jj)::value;
               sum[J] = fmaf(cf, acc.template at<2 * TI + TX, DY, DX, J>(), sum[J]);
