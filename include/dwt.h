@@ -139,7 +139,7 @@ dwt_status dwt_plan_set_tile(dwt_plan plan, int strip_rows, int stages);
  * which each level is cut into 2-D tiles held in shared memory (one
  * barrier per step that reads other quadruples) and the levels are
  * separated by a grid-wide barrier.  The larger levels keep one streaming
- * launch each.  -1 restores the default (2048 x 2048 samples), 0 turns the
+ * launch each.  -1 restores the default (512 x 512 samples), 0 turns the
  * fusion off.  Row-column and Convolution plans never fuse.  The result is
  * the same transform (float: within rounding of the per-level kernels;
  * int32: bit-identical).  Errors: DWT_EINVAL for values below -1. */
