@@ -714,7 +714,7 @@ struct Tile {
 dwt_status level_geometry(const Tile& t, const LaunchKey& key, LevelArgs& a, KernelInfo& ki) {
   if (!find_kernel(key, t.nstages, &ki)) return DWT_EUNSUPPORTED;
   const Occ oc = occupancy(ki, t.device);
-  const int cap = oc.sms * oc.per_sm;
+  const int cap = oc.sms * oc.per_sm * kWarpsPerCta;  // resident warps (strips)
   // one strip per resident warp when the level is large enough: a single
   // wave, with strips as tall as that allows (less vertical halo)
   a.ncs = (a.cw + ki.uq - 1) / ki.uq;
@@ -728,7 +728,7 @@ dwt_status level_geometry(const Tile& t, const LaunchKey& key, LevelArgs& a, Ker
   a.nstages = t.nstages;
   if (t.nstages < kMaxStages && (long long)a.ncs * a.nrs < cap) {
     const Occ deep = occupancy(ki.fn, smem_with_stages(ki, t.nstages, kMaxStages), t.device);
-    if ((long long)a.ncs * a.nrs <= (long long)deep.sms * deep.per_sm) a.nstages = kMaxStages;
+    if ((long long)a.ncs * a.nrs <= (long long)deep.sms * deep.per_sm * kWarpsPerCta) a.nstages = kMaxStages;
   }
   return DWT_OK;
 }
@@ -1235,7 +1235,7 @@ dwt_status batch_submit(const dwt_request* reqs, int n, cudaStream_t s, int* d_s
   KernelInfo kinfo[BK_COUNT];
   for (int k = 0; k < BK_COUNT; ++k)
     if (!batch_kind_info(k, &kinfo[k])) return DWT_EUNSUPPORTED;
-  const Occ oc = occupancy(kinfo[0], device);
+  const Occ oc = occupancy(kinfo[0].fn, kinfo[0].smem_bytes, device, 32);  // one-warp blocks
   const int resident = oc.sms * oc.per_sm;
 
   // ring depth: the deepest any plan whose tile the caller set asks for,

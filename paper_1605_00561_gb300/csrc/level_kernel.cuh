@@ -776,6 +776,11 @@ __device__ __forceinline__ bool run_strip(const LevelArgs& a, const TmaMaps& map
   const int q_end = q0 + rows_out;
   const uint32_t g0 = chunk_ctr;
   for (int c = 0; c < NS - 1 && c < nchunks; ++c) sp.fill(c, (g0 + c) % NS);
+  // stage and phase of the chunk being consumed, advanced by one per chunk
+  // (no division by the run-time ring depth inside the loop); the chunk
+  // filled while it is consumed goes to the stage consumed just before
+  int s = (int)(g0 % (uint32_t)NS);
+  uint32_t phase = (g0 / (uint32_t)NS) & 1u;
 
   const typename Strip<C>::Out ob = sp.out_bases();
   const typename Strip<C>::Remap remap = sp.remap_cols();
@@ -786,11 +791,9 @@ __device__ __forceinline__ bool run_strip(const LevelArgs& a, const TmaMaps& map
     const int cn = c + NS - 1;
     if (cn < nchunks) {
       __syncwarp();
-      sp.fill(cn, (g0 + cn) % NS);
+      sp.fill(cn, s == 0 ? NS - 1 : s - 1);
     }
-    const uint32_t g = g0 + c;
-    const int s = g % NS;
-    bool ok = ptx::mbar_wait_bounded(&bars[s], (g / NS) & 1, a.probes);
+    bool ok = ptx::mbar_wait_bounded(&bars[s], phase, a.probes);
     ok = __all_sync(kFull, ok);
     if (!ok) {
       if (lane == 0) atomicOr(a.status, 1);
@@ -811,6 +814,10 @@ __device__ __forceinline__ bool run_strip(const LevelArgs& a, const TmaMaps& map
       const Row<typename C::VT, C::QL> out = pipe.push(in, coefs, ct);
       const int q = qc + r;
       if (q >= q0 && q < q_end) sp.store_row(ob, out, q);
+    }
+    if (++s == NS) {
+      s = 0;
+      phase ^= 1u;
     }
   }
   chunk_ctr = g0 + nchunks;
