@@ -165,6 +165,7 @@ void kind_info(KernelInfo* k) {
   k->smem_bytes = batch_smem_bytes();
   k->fn = reinterpret_cast<const void*>(&batch_kernel<false>);
   k->supported = true;
+  k->realign = C::REALIGN;
 }
 
 }  // namespace

@@ -389,18 +389,42 @@ bool encode_2d(CUtensorMap* m, int dtype, const void* base, int w, int h, size_t
 // valid (bit p for plane p): the kernels load those by TMA and copy the
 // others (a plane whose base or row pitch is not 16-byte aligned, as the HL
 // and HH bands at column ceil(w/2) of most odd-width coefficient planes).
-int encode_level_maps(TmaMaps* maps, int dtype, const LevelArgs& a, const KernelInfo& ki, size_t es) {
+//
+// A subband plane whose rows are 16-byte multiples but whose first element
+// is not 16-byte aligned (HL and HH at column ceil(w/2) of padded rows)
+// gets a map anchored at the aligned column before it, `off` elements
+// earlier and `off` columns wider, when the kernel takes such planes
+// (ki.realign); a.src_off records the offset.  Only HL and HH (the odd
+// column parity) are realigned, and both must share the offset (one box
+// geometry in the kernel); LL and LH start at column 0 of their rows.
+int encode_level_maps(TmaMaps* maps, int dtype, LevelArgs& a, const KernelInfo& ki, size_t es) {
   std::memset(maps, 0, sizeof *maps);
+  for (int i = 0; i < 4; ++i) a.src_off[i] = 0;
   if (a.W < 2 || a.H < 2) return 0;
   if (ki.load == SAMPLES)
     return encode_2d(&maps->m[0], dtype, a.src[0], a.W, a.H, (size_t)a.src_pitch[0] * es, ki.box_w, ki.box_h)
                ? 1
                : 0;
   const int pw[4] = {a.cw, a.fw, a.cw, a.fw}, ph[4] = {a.ch, a.ch, a.fh, a.fh};
+  // only the odd-parity planes (HL, HH) are realigned: the even ones start
+  // at column 0 of their rows
+  int off[4] = {0, 0, 0, 0};
+  if (ki.realign)
+    for (int i = 1; i < 4; i += 2) {
+      const uintptr_t b = reinterpret_cast<uintptr_t>(a.src[i]);
+      if ((((size_t)a.src_pitch[i] * es) & 15) == 0 && b % es == 0) off[i] = (int)((b & 15) / es);
+    }
+  if (off[1] != off[3]) off[1] = off[3] = 0;
   int mask = 0;
-  for (int i = 0; i < 4; ++i)
-    if (encode_2d(&maps->m[i], dtype, a.src[i], pw[i], ph[i], (size_t)a.src_pitch[i] * es, ki.box_w, ki.box_h))
+  for (int i = 0; i < 4; ++i) {
+    const void* base = static_cast<const char*>(a.src[i]) - (size_t)off[i] * es;
+    if (encode_2d(&maps->m[i], dtype, base, pw[i] + off[i], ph[i], (size_t)a.src_pitch[i] * es, ki.box_w, ki.box_h)) {
       mask |= 1 << i;
+      a.src_off[i] = off[i];
+    }
+  }
+  // realigned only if both odd-parity planes got their maps
+  if (a.src_off[1] != a.src_off[3]) a.src_off[1] = a.src_off[3] = 0;
   return mask;
 }
 

@@ -89,6 +89,11 @@ struct LevelArgs {
   void* dst[4];
   long long dst_pitch[4];
   int src_tma;   // bit p: the tensor map of source plane p is valid (TMA loads it)
+  // Subband sources: elements between plane p's first element and the
+  // 16-byte-aligned column before it where its tensor map starts (0: the
+  // plane starts aligned, or is not loaded realigned).  Only HL and HH
+  // (planes 1 and 3, the same offset) are realigned.
+  int src_off[4];
   int* status;   // device error word (bit 0: a bounded wait ran out)
   uint32_t probes;  // limit of a ring-stage wait (mbarrier probes)
   uint32_t spins;   // limit of a row-counter or flag wait (polls)
@@ -114,6 +119,7 @@ struct KernelInfo {
   size_t smem_bytes;
   const void* fn;  // kernel entry (for occupancy queries)
   bool supported;
+  bool realign;  // loads subband planes from the aligned column before a misaligned start
 };
 
 struct LaunchKey {

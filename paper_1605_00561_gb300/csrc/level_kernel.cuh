@@ -144,6 +144,17 @@ struct Cfg {
   static constexpr int NPLANES = LOAD == SAMPLES ? 1 : 4;
   static constexpr int STAGE_BYTES = NPLANES * PLANE_BYTES;
   static_assert(ROWE <= 256, "TMA box wider than 256 elements");
+  // A subband plane whose start is not 16-byte aligned while its rows are
+  // (HL and HH at column ceil(w/2) of coefficient rows padded to 16 bytes)
+  // is loaded by TMA from the aligned column at or before its start (the
+  // tensor map is anchored there: no box coordinate is ever unaligned).  A
+  // box with A - 1 columns of room takes the shift as it is; a box exactly
+  // as wide as the span takes it when the halo quadruples the stencil never
+  // reads (HQ - LEFT on the left, HQ - RIGHT on the right) cover A - 1
+  // columns, by starting the box up to HQ - RIGHT columns late.
+  static constexpr bool WIDE_BOX = ROWE >= SPAN + A - 1;
+  static constexpr bool REALIGN =
+      LOAD == SUBBANDS && (WIDE_BOX || 2 * HQ - Tot::LEFT - Tot::RIGHT >= A - 1);
   static_assert(UQ > 0 && HQ <= 2 * QL, "halo too wide for the lane layout");
 };
 
@@ -175,6 +186,37 @@ struct Strip {
   uint64_t* bars;
   int stride = C::STAGE_BYTES;  // bytes between ring stages
   bool box = false;             // chunks land in the TMA box layout (see boxed())
+  // Subband planes of odd column parity (HL and HH, planes 1 and 3, which
+  // share one offset; the even planes start at column 0 of their rows in
+  // every layout and are never realigned): the first column of their box
+  // in tensor-map coordinates (x1).  A realigned strip (box and a nonzero
+  // a.src_off[1]) starts that map a.src_off[1] columns before the planes'
+  // first element; otherwise map and plane columns coincide.
+  int x1 = 0;
+
+  __device__ __forceinline__ int offu(int px) const {
+    if constexpr (C::REALIGN) return (px && box) ? a.src_off[1] : 0;
+    else return 0;
+  }
+  // plane column at shared-memory column 0 of a box row of parity px
+  __device__ __forceinline__ int be(int px) const {
+    if constexpr (C::REALIGN) return px ? x1 - offu(1) : align_down(mfirst, C::A);
+    else return align_down(mfirst, C::A);
+  }
+
+  // Box columns of the odd-parity planes: with `realign`, from the offset
+  // the host encoded their tensor maps with (a.src_off[1]), else from the
+  // planes' own starts.  Called before `box` is decided (with realign) and
+  // again if the strip does not take the box layout (without).
+  __device__ __forceinline__ void set_box_cols(bool realign) {
+    if constexpr (C::REALIGN) {
+      const int off = realign ? a.src_off[1] : 0;
+      int x = align_down(mfirst + off, C::A);
+      if (!C::WIDE_BOX && off != 0 && mfirst + off - x > C::HQ - C::Tot::RIGHT) x += C::A;
+      x1 = x;
+      box = realign;  // offu() reads the offset while boxed() decides
+    }
+  }
 
   __device__ __forceinline__ ST* plane(int s, int p) const {
     return reinterpret_cast<ST*>(sm + (size_t)s * stride + p * C::PLANE_BYTES);
@@ -210,7 +252,7 @@ struct Strip {
     if constexpr (C::LOAD == SAMPLES) {
       return mirror(x, a.W) - align_down(2 * mfirst, C::A);
     } else {
-      return (mirror(2 * x + px, a.W) >> 1) - align_down(mfirst, C::A);
+      return (mirror(2 * x + px, a.W) >> 1) - be(px);
     }
   }
   __device__ __forceinline__ bool cols_by_tma() const {
@@ -289,10 +331,13 @@ struct Strip {
     if constexpr (C::LOAD == SAMPLES) {
       return box_copyable(a.src[0], a.src_pitch[0]);
     } else {
-      return box_copyable(a.src[0], a.src_pitch[0]) && box_copyable(a.src[1], a.src_pitch[1]) &&
-             box_copyable(a.src[2], a.src_pitch[2]) && box_copyable(a.src[3], a.src_pitch[3]);
+      return box_copyable(copy_base(0), a.src_pitch[0]) && box_copyable(copy_base(1), a.src_pitch[1]) &&
+             box_copyable(copy_base(2), a.src_pitch[2]) && box_copyable(copy_base(3), a.src_pitch[3]);
     }
   }
+  // Where box copies of subband plane p start: the column its tensor map
+  // starts at (offu(p & 1) columns before the plane's first element).
+  __device__ __forceinline__ const ST* copy_base(int p) const { return src_plane(p) - offu(p & 1); }
 
   __device__ void fill(int c, int s) const {
     const int y0 = yfirst + c * C::CH;
@@ -361,13 +406,13 @@ struct Strip {
       // four subband planes; the lane covers quads mfirst + QL*lane + (0..QL-1)
       const int tma = a.src_tma & 15;
       if (box && tma && y0 >= 0 && y0 + C::CH <= a.fh) {
-        const int x0 = align_down(mfirst, C::A);
         if (tma == 15) {
           if (lane == 0) {
             ptx::fence_proxy_async_smem();
             ptx::mbar_arrive_expect_tx(bar, 4 * C::BOX_BYTES);
 #pragma unroll
-            for (int p = 0; p < 4; ++p) ptx::tma_load_2d(plane(s, p), &maps.m[p], x0, y0, bar);
+            for (int p = 0; p < 4; ++p)
+              ptx::tma_load_2d(plane(s, p), &maps.m[p], be(p & 1) + offu(p & 1), y0, bar);
           } else {
             ptx::mbar_arrive(bar);
           }
@@ -382,21 +427,22 @@ struct Strip {
           ptx::mbar_expect_tx(bar, (uint32_t)__popc(tma) * C::BOX_BYTES);
 #pragma unroll
           for (int p = 0; p < 4; ++p)
-            if ((tma >> p) & 1) ptx::tma_load_2d(plane(s, p), &maps.m[p], x0, y0, bar);
+            if ((tma >> p) & 1) ptx::tma_load_2d(plane(s, p), &maps.m[p], be(p & 1) + offu(p & 1), y0, bar);
         }
 #pragma unroll 1
         for (int p = 0; p < 4; ++p) {
           if ((tma >> p) & 1) continue;
-          const int pw = (p & 1) ? a.fw : a.cw;
+          const int px = p & 1;
+          const int pw = px ? a.fw : a.cw;
 #pragma unroll 1
           for (int r = 0; r < C::CH; ++r)
-            copy_box_row(plane(s, p) + r * C::ROWE, src_plane(p) + (long long)(y0 + r) * a.src_pitch[p], x0, pw);
+            copy_box_row(plane(s, p) + r * C::ROWE, copy_base(p) + (long long)(y0 + r) * a.src_pitch[p],
+                         be(px) + offu(px), pw + offu(px));
         }
         ptx::cp_async_arrive(bar);
         return;
       }
       if (box) {
-        const int x0 = align_down(mfirst, C::A);
 #pragma unroll 1
         for (int p = 0; p < 4; ++p) {
           const int py = p >> 1, px = p & 1;
@@ -407,7 +453,8 @@ struct Strip {
             // mirroring keeps the parity of a sample index: a mirrored row
             // of plane p is again a row of plane p
             const int iy = (y >= 0 && y < ph) ? y : (mirror(2 * y + py, a.H) >> 1);
-            copy_box_row(plane(s, p) + r * C::ROWE, src_plane(p) + (long long)iy * a.src_pitch[p], x0, pw);
+            copy_box_row(plane(s, p) + r * C::ROWE, copy_base(p) + (long long)iy * a.src_pitch[p],
+                         be(px) + offu(px), pw + offu(px));
           }
         }
         ptx::cp_async_arrive(bar);
@@ -527,6 +574,20 @@ struct Strip {
 
   __device__ __forceinline__ Remap remap_cols() const {
     Remap rm{false, {0u, 0u}, 0u};
+    if constexpr (C::REALIGN) {
+      // a realigned strip whose odd planes sit at other box columns than the
+      // even ones: every lane reads its elements one by one (columns clamped
+      // into the row; the clamped ones are halo elements no stored value
+      // reads); border lanes are remapped below as usual
+      if (box && be(1) != be(0)) {
+        rm.on = true;
+#pragma unroll
+        for (int px = 0; px < 2; ++px)
+#pragma unroll
+          for (int t = 0; t < QL; ++t)
+            rm.col[px] |= (uint32_t)min(max(mfirst - be(px) + QL * lane + t, 0), C::ROWE - 1) << (8 * t);
+      }
+    }
     if (!box || cols_inside()) return rm;
     if constexpr (C::LOAD == SAMPLES) {
       const int xs = 2 * mfirst, xal = align_down(xs, C::A), x0 = xs + 2 * QL * lane;
@@ -541,9 +602,10 @@ struct Strip {
         rm.col[t / 4] |= c << (8 * (t % 4));
       }
     } else {
-      const int xal = align_down(mfirst, C::A), m = mfirst + QL * lane;
-      rm.on = m < 0 || m + QL > a.fw;
-      if (!rm.on) return rm;
+      const int m = mfirst + QL * lane;
+      if (m >= 0 && m + QL <= a.fw) return rm;
+      rm.on = true;
+      rm.col[0] = rm.col[1] = 0u;
 #pragma unroll
       for (int px = 0; px < 2; ++px) {
         const int pw = px ? a.fw : a.cw;
@@ -553,7 +615,7 @@ struct Strip {
           uint32_t c = 0;
           if (mm >= -C::HQ && mm <= pw + C::HQ) {
             const int sm_ = (mm >= 0 && mm < pw) ? mm : (mirror(2 * mm + px, a.W) >> 1);
-            c = (uint32_t)min(max(sm_ - xal, 0), C::ROWE - 1);
+            c = (uint32_t)min(max(sm_ - be(px), 0), C::ROWE - 1);
           } else {
             rm.zero |= 1u << (QL * px + t);
           }
@@ -767,7 +829,12 @@ __device__ __forceinline__ bool run_strip(const LevelArgs& a, const TmaMaps& map
   using Tot = typename C::Tot;
   Strip<C> sp{a, maps, lane, cs * C::UQ, cs * C::UQ - C::HQ, q0 - Tot::UP, ring, bars};
   sp.stride = stage_stride;
-  sp.box = sp.boxed();
+  // the box layout with the planes' realignment, if the strip can take it;
+  // otherwise lane copies, which read every plane from its own start
+  sp.set_box_cols(true);
+  const bool boxed = sp.boxed();
+  if (!boxed) sp.set_box_cols(false);
+  sp.box = boxed;
 
   // rows streamed: the strip plus its halo, padded to whole chunks (the
   // extra rows are mirrored image rows, lifted but never stored)
@@ -878,6 +945,7 @@ struct Instance {
     k.smem_bytes = smem(nstages);
     k.fn = reinterpret_cast<const void*>(&level_kernel<C>);
     k.supported = true;
+    k.realign = C::REALIGN;
     return k;
   }
   static cudaError_t launch(const LevelArgs& a, const TmaMaps& m, const Coefs& cf,
