@@ -11,8 +11,9 @@
 // warp shuffles.  What the paper synchronises with a work-group barrier
 // between two steps is, here, the hand-over of a row from one stage's
 // output to the next stage's window (vertical) and a shuffle (horizontal);
-// no CTA-wide barrier is needed.  Strips are numbered row-major over the
-// level and four consecutive strips form a CTA, so every CTA is full.
+// no CTA-wide barrier is needed.  Each strip is a one-warp CTA (kWarpsPerCta
+// consecutive strips per CTA in general; more per CTA measured no faster),
+// dispatched border columns first (strip_coords).
 //
 // Loads.  Rows arrive in chunks of CH quad rows through a per-warp ring of
 // shared-memory stages, filled ahead of use: a chunk lying inside the image
