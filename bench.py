@@ -92,16 +92,27 @@ SCHEME_SOURCE = {"rowcol": "k_rowcol.cu", "sweldens": "k_sweldens.cu", "iwahashi
 ALL_SCHEMES = list(SCHEME_SOURCE)
 
 
+def _code_only(text):
+    """Source text without // comments and blank lines (a comment edit does
+    not change the kernels)."""
+    out = []
+    for line in text.splitlines():
+        code = line.split("//", 1)[0].rstrip()
+        if code.strip():
+            out.append(code)
+    return "\n".join(out)
+
+
 def kernel_source_hash(scheme="monolithic*"):
-    """Hash of the sources of one scheme's per-level kernels: DRAM traffic
+    """Hash of the code of one scheme's per-level kernels: DRAM traffic
     recorded for an older version of them no longer applies."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1605_00561_gb300", "csrc")
     for f in LEVEL_KERNEL_SOURCES + [SCHEME_SOURCE.get(scheme, "")]:
         path = os.path.join(csrc, f)
         if os.path.isfile(path):
-            with open(path, "rb") as fh:
-                h.update(f.encode() + fh.read())
+            with open(path, encoding="utf-8") as fh:
+                h.update(f.encode() + _code_only(fh.read()).encode())
     return h.hexdigest()[:16]
 
 
