@@ -114,3 +114,47 @@ def test_fuzz_against_oracle(dwt, case):
         assert np.abs(c.astype(np.float64) - ref).max() <= tol, "forward: " + what
         assert np.abs(yo.astype(np.float64) - x).max() <= tol, "inverse of oracle coefficients: " + what
         assert np.abs(y.astype(np.float64) - x).max() <= 2 * tol, "round trip: " + what
+
+
+def test_fuzz_batch_against_oracle(dwt):
+    """48 seeded random requests in one batch: sizes 1-709, every level
+    count, CDF 5/3, 9/7 and DD 13/7 in float32 and the integer 5/3, both
+    directions, packed and padded pitches.  A batch runs Monolithic* for
+    float and the JPEG 2000 order for int32, whatever scheme a plan names."""
+    rng = np.random.default_rng(4120)
+    reqs, keep, checks, plans = [], [], [], []
+    for i in range(48):
+        h, w = (int(np.clip(np.round(np.exp(rng.uniform(0.0, np.log(720.0)))), 1, 720)) for _ in range(2))
+        kind = "int53" if rng.random() < 0.3 else "float"
+        wavelet = "cdf53" if kind == "int53" else str(rng.choice(["cdf53", "cdf97", "dd137"]))
+        L = int(rng.integers(0, oracle.max_levels(w, h) + 1))
+        inverse = bool(rng.random() < 0.5)
+        pad = str(rng.choice(["packed", "16", "128", "odd"]))
+        if kind == "float":
+            x = inputs.uniform_image(h, w, seed=500 + i)
+            ref = oracle.dwt2(x.astype(np.float64), OID[wavelet], L)
+            dtype, tdt = "f32", torch.float32
+        else:
+            x = inputs.int12_image(h, w, seed=500 + i)
+            ref = oracle.dwt2_int(x, L)
+            dtype, tdt = "i32", torch.int32
+        p = dwt.Plan(w, h, wavelet, L, dtype, scheme=str(rng.choice(FLOAT_SCHEMES)) if kind == "float" else "sweldens")
+        src = buffer(ref if inverse else x, tdt, pad)
+        dst = buffer(np.zeros((h, w)), tdt, pad)
+        reqs.append(p.request(src, dst, inverse=inverse))
+        keep.append((src, dst))
+        plans.append(p)
+        checks.append((dst, x if inverse else ref, dtype, L,
+                       f"request {i}: h={h} w={w} L={L} {kind} {wavelet} {'inv' if inverse else 'fwd'} pitch={pad}"))
+    status = torch.zeros(len(reqs), dtype=torch.int32, device="cuda")
+    dwt.submit(reqs, status=status)
+    torch.cuda.synchronize()
+    assert int(status.abs().max()) == 0
+    for dst, want, dtype, L, what in checks:
+        got = dst.cpu().numpy()
+        if dtype == "i32":
+            assert np.array_equal(got, want), what
+        else:
+            assert np.abs(got.astype(np.float64) - want).max() <= TOL_F32 * max(1.0, L / 6.0), what
+    for p in plans:
+        p.close()
