@@ -14,6 +14,11 @@
  *     of the element size, as are the plane addresses).  Device pointers
  *     must be CUDA device (or managed) memory; host pointers are rejected
  *     with DWT_EINVAL, never dereferenced on the GPU.
+ *   - Speed: planes whose row pitch is a multiple of 16 bytes are loaded by
+ *     the TMA engine, the HL and HH bands of odd widths included; rows of
+ *     odd widths packed without padding cannot be, and are copied by the
+ *     threads (for 5001 x 3333 float32, 1.3-1.4x slower; float16 inverse
+ *     2.9x).  Padding rows to 128 bytes, as cudaMallocPitch does, avoids it.
  *   - Output layout (forward) / input layout (inverse): Mallat packing of a
  *     w x h plane.  At level k the level's input is W_k x H_k (W_0 = w,
  *     W_{k+1} = ceil(W_k / 2)); its LL band is ceil(W_k/2) x ceil(H_k/2) at
