@@ -229,6 +229,57 @@ def cpu_baseline_oracle(a, n=None, reps=2):
     return 2.0 * n * n * reps / dt / 1e9, dt, n
 
 
+def _oracle_replica(n, wavelet, levels, seed, barrier, out):
+    """One process of the all-cores baseline: the oracle, forward then
+    inverse, on its own n x n image; the transforms of all processes start
+    together at `barrier` and each reports its own duration."""
+    import numpy as np
+
+    import oracle
+    from paper_1605_00561_gb300 import inputs
+    oid = oracle.CDF97 if wavelet == "cdf97" else oracle.CDF53
+    x = inputs.textured_image(n, n, seed=seed).astype(np.float64)
+    barrier.wait(timeout=600)
+    t = time.perf_counter()
+    c = oracle.dwt2(x, oid, levels)
+    oracle.dwt2(c, oid, levels, inverse=True)
+    out.put(time.perf_counter() - t)
+
+
+def cpu_baseline_all_cores(a, n=4096):
+    """The same oracle on every host core at once: one process per core, each
+    transforming its own n x n image (independent images; the oracle itself
+    is unchanged and single-threaded).  Returns (Gpixel/s of all processes
+    over the slowest one's duration, that duration, processes), or None if
+    a process failed.  Processes are spawned, never forked: the parent holds
+    a CUDA context."""
+    import multiprocessing as mp
+    import queue
+
+    procs = os.cpu_count() or 1
+    ctx = mp.get_context("spawn")
+    barrier, out = ctx.Barrier(procs), ctx.Queue()
+    ps = [ctx.Process(target=_oracle_replica, args=(n, a.wavelet, a.levels, 11 + i, barrier, out))
+          for i in range(procs)]
+    for p in ps:
+        p.start()
+    times, deadline = [], time.time() + 900
+    while len(times) < procs and time.time() < deadline:
+        try:
+            times.append(out.get(timeout=1.0))
+        except queue.Empty:
+            if not any(p.is_alive() for p in ps):
+                break
+    for p in ps:
+        p.join(timeout=10)
+        if p.is_alive():
+            p.terminate()
+    if len(times) < procs:
+        return None
+    slowest = max(times)
+    return 2.0 * n * n * procs / slowest / 1e9, slowest, procs
+
+
 def run_reference(a, rank, world):
     """The reference arm: the oracle as it stands (plain C, FP64, one thread)
     timed on the host cores, on rank 0 only.  Each step transforms one
@@ -882,6 +933,12 @@ def main():
         cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"{nn}x{nn} forward + inverse, twice ({dt:.1f} s), FP64 C oracle, 1 thread",
                "host": host_cpu()}
+        allc = cpu_baseline_all_cores(a)
+        if allc is not None:
+            va, dta, procs = allc
+            cpu["all_cores"] = {"value": va, "unit": UNIT, "cores": procs, "kind": "oracle",
+                                "sample": f"{procs} processes at once, each its own 4096x4096 image forward + "
+                                          f"inverse (slowest {dta:.1f} s), the same single-threaded oracle"}
 
     if rank == 0:
         print(json.dumps({
