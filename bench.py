@@ -933,11 +933,11 @@ def main():
         cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"{nn}x{nn} forward + inverse, twice ({dt:.1f} s), FP64 C oracle, 1 thread",
                "host": host_cpu()}
-        allc = cpu_baseline_all_cores(a)
+        allc = cpu_baseline_all_cores(a, n=nn)
         if allc is not None:
             va, dta, procs = allc
             cpu["all_cores"] = {"value": va, "unit": UNIT, "cores": procs, "kind": "oracle",
-                                "sample": f"{procs} processes at once, each its own 4096x4096 image forward + "
+                                "sample": f"{procs} processes at once, each its own {nn}x{nn} image forward + "
                                           f"inverse (slowest {dta:.1f} s), the same single-threaded oracle"}
 
     if rank == 0:
