@@ -9,7 +9,20 @@ within the 8-bit-range bar, which is stated for up to six levels: deeper
 pyramids (up to ten levels here) add one rounding of the LL band per
 level, so the bar scales with L / 6 beyond six (the unstarred Polyphase
 9/7 round trip reaches 4.7e-3 at ten levels).  A failure message carries
-the configuration."""
+the configuration.
+
+A second, wider set (``DWT_FUZZ_WIDE`` cases, 240 by default) adds the
+paper's zeta normalisation, float16 storage, the host-buffer calls,
+autotuned plans, fusion thresholds between 64 x 64 and 1024 x 1024 and
+sides up to 2600.  Float16 storage is held to 1 + 0.3 L (+ 2e-3 of the
+largest coefficient), between its measured error (0.30 after three levels
+of 9/7) and the worst case: every level rounds each band once (at most
+0.125 for values under 512, half the float16 spacing there), and the
+following levels' filters amplify it (l1 norms per axis 1.38 for the 9/7
+lowpass, 2.6 for the highpass).  The unstarred Polyphase 9/7 has a bar of
+its own (TOL_F32_POLYPHASE97)."""
+import os
+
 import numpy as np
 import pytest
 
@@ -158,3 +171,170 @@ def test_fuzz_batch_against_oracle(dwt):
             assert np.abs(got.astype(np.float64) - want).max() <= TOL_F32 * max(1.0, L / 6.0), what
     for p in plans:
         p.close()
+
+
+NWIDE = int(os.environ.get("DWT_FUZZ_WIDE", "240"))
+TDT = {"f32": torch.float32, "f16s": torch.float16, "i32": torch.int32}
+
+
+def wide_cases():
+    rng = np.random.default_rng(20261205)
+    out = []
+    for i in range(NWIDE):
+        hi = 2600 if rng.random() < 0.1 else 700
+        side = lambda: int(np.clip(np.round(np.exp(rng.uniform(0.0, np.log(hi)))), 1, hi))
+        h, w = side(), side()
+        if rng.random() < 0.06:
+            h = 1 if rng.random() < 0.5 else h
+            w = 1 if h != 1 else w
+        kind = str(rng.choice(["f32", "f32", "zeta", "f16s", "i32", "intiw"]))
+        if kind in ("f32", "zeta"):
+            wavelet, scheme = str(rng.choice(["cdf53", "cdf97", "dd137"])), str(rng.choice(FLOAT_SCHEMES))
+        elif kind == "f16s":
+            wavelet, scheme = str(rng.choice(["cdf53", "cdf97"])), str(rng.choice(FLOAT_SCHEMES))
+        elif kind == "i32":
+            wavelet, scheme = "cdf53", str(rng.choice(["sweldens", "rowcol"]))
+        else:
+            wavelet, scheme = "cdf53", "iwahashi"
+        L = int(rng.integers(0, oracle.max_levels(w, h) + 1))
+        pad = str(rng.choice(["packed", "16", "128", "odd"]))
+        fusion = int(rng.choice([-1, 0, 4096, 1 << 20]))
+        rows = int(rng.choice([0, 0, 0, 2, 5, 10, 16, 33]))
+        stages = int(rng.choice([0, 0, 1, 2, 3, 4]))
+        path = str(rng.choice(["device", "device", "device", "host", "autotune"]))
+        out.append((i, h, w, L, kind, wavelet, scheme, pad, fusion, rows, stages, path))
+    return out
+
+
+def wide_image(kind, h, w, seed):
+    if kind in ("i32", "intiw"):
+        return inputs.int12_image(h, w, seed=seed)
+    x = inputs.uniform_image(h, w, seed=seed)
+    return x.astype(np.float16).astype(np.float32) if kind == "f16s" else x
+
+
+def wide_reference(x, kind, wavelet, L):
+    if kind == "i32":
+        return oracle.dwt2_int(x, L)
+    if kind == "intiw":
+        return oracle.dwt2_int_iwahashi(x, L)
+    norm = oracle.NORM_ZETA if kind == "zeta" else oracle.NORM_JPEG2000
+    return oracle.dwt2(x.astype(np.float64), OID[wavelet], L, norm=norm)
+
+
+# The unstarred Polyphase scheme with CDF 9/7 evaluates each merged step
+# V = PU + 1 as one 2-D FIR: about 20 float32 roundings per output and step
+# at magnitudes up to ~1000 (centre tap (1 + 2 gamma delta)^2 = 3.18 for the
+# second pair), against about 6 for a lifting pair.  Measured on 8-bit
+# noise: 1.0e-3 after one level (the lifting schemes 3-7e-4) and up to
+# 2.2e-3 after five or six levels, so it misses the 2e-3 bar by up to 10 %;
+# its own bar is 2.5e-3.  (DD 13/7, with dyadic coefficients, stays near
+# 1e-4 in every scheme.)
+TOL_F32_POLYPHASE97 = 2.5e-3
+
+
+def wide_tol(kind, L, ref, base=TOL_F32):
+    big = float(np.abs(ref).max(initial=0.0))
+    if kind == "f16s":
+        return 1.0 + 0.3 * L + 2e-3 * big
+    # float32: the 8-bit-range bar, relative for the zeta normalisation's
+    # larger coefficients
+    return max(base, 8e-6 * big) * max(1.0, L / 6.0)
+
+
+def assert_close(got, want, kind, L, what, factor=1.0, base=TOL_F32):
+    if kind in ("i32", "intiw"):
+        assert np.array_equal(got, want), what
+    else:
+        err = float(np.abs(got.astype(np.float64) - want).max(initial=0.0))
+        assert err <= factor * wide_tol(kind, L, want, base), f"{what}: max|err| {err}"
+
+
+@pytest.mark.parametrize("case", wide_cases(), ids=lambda c: f"w{c[0]}")
+def test_wide_fuzz_against_oracle(dwt, case):
+    i, h, w, L, kind, wavelet, scheme, pad, fusion, rows, stages, path = case
+    what = (f"h={h} w={w} L={L} {kind} {wavelet} {scheme} pitch={pad} fusion={fusion} rows={rows} "
+            f"stages={stages} {path}")
+    dtype = "i32" if kind in ("i32", "intiw") else ("f16s" if kind == "f16s" else "f32")
+    x = wide_image(kind, h, w, 3000 + i)
+    ref = wide_reference(x, kind, wavelet, L)
+    plan = dwt.Plan(w, h, wavelet, L, dtype, scheme=scheme)
+    try:
+        if kind == "zeta":
+            dwt.dwt_plan_set_normalization(plan.handle, dwt.DWT_NORM_ZETA)
+        dwt.dwt_plan_set_fusion(plan.handle, fusion)
+        if rows or stages:
+            dwt.dwt_plan_set_tile(plan.handle, rows, stages)
+        tdt = TDT[dtype]
+        dev = "cpu" if path == "host" else "cuda"
+        xd = buffer(x, tdt, pad).to(dev) if dev == "cuda" else host_buffer(x, tdt, pad)
+        c = buffer(np.zeros((h, w)), tdt, pad) if dev == "cuda" else host_buffer(np.zeros((h, w)), tdt, pad)
+        y = buffer(np.zeros((h, w)), tdt, pad) if dev == "cuda" else host_buffer(np.zeros((h, w)), tdt, pad)
+        if path == "host":
+            plan.forward_host(xd, c)
+            plan.inverse_host(c, y)
+        else:
+            if path == "autotune":
+                dwt.dwt_plan_autotune(plan.handle)
+                what += f" (tuned: {plan.scheme})"
+            plan.forward(xd, c)
+            plan.inverse(c, y)
+            co = buffer(ref, tdt, pad)
+            yo = buffer(np.zeros((h, w)), tdt, pad)
+            plan.inverse(co, yo)
+        torch.cuda.synchronize()
+        assert dwt.dwt_plan_device_status(plan.handle) == dwt.DWT_OK, what
+        base = TOL_F32_POLYPHASE97 if (plan.scheme == "polyphase" and wavelet == "cdf97") else TOL_F32
+        assert_close(c.cpu().numpy(), ref, kind, L, "forward: " + what, base=base)
+        assert_close(y.cpu().numpy(), x, kind, L, "round trip: " + what, 2.0, base=base)
+        if path != "host":
+            assert_close(yo.cpu().numpy(), x, kind, L, "inverse of oracle coefficients: " + what, base=base)
+    finally:
+        plan.close()
+
+
+def host_buffer(a, tdt, pad):
+    """A host (pageable) copy of `a` with rows laid out per `pad`."""
+    h, w = a.shape
+    es = torch.empty((), dtype=tdt).element_size()
+    pitch = w if pad == "packed" else (w + 3 if pad == "odd" else -(-w * es // int(pad)) * int(pad) // es)
+    buf = torch.zeros(h, pitch, dtype=tdt)
+    buf[:, :w] = torch.from_numpy(np.ascontiguousarray(a)).to(tdt)
+    return buf[:, :w]
+
+
+def test_wide_fuzz_batches_with_float16(dwt):
+    """Four seeded batches of 1-40 random requests mixing float32 (CDF 5/3,
+    9/7, DD 13/7), float16 storage (CDF 5/3, 9/7) and int32, both
+    directions, every pitch kind."""
+    rng = np.random.default_rng(8080)
+    for b in range(4):
+        reqs, keep, checks, plans = [], [], [], []
+        for j in range(int(rng.integers(1, 41))):
+            h, w = (int(np.clip(np.round(np.exp(rng.uniform(0.0, np.log(900.0)))), 1, 900)) for _ in range(2))
+            kind = str(rng.choice(["f32", "f32", "f16s", "i32"]))
+            wavelet = "cdf53" if kind == "i32" else str(
+                rng.choice(["cdf53", "cdf97", "dd137"] if kind == "f32" else ["cdf53", "cdf97"]))
+            L = int(rng.integers(0, oracle.max_levels(w, h) + 1))
+            inverse = bool(rng.random() < 0.5)
+            pad = str(rng.choice(["packed", "16", "128", "odd"]))
+            x = wide_image(kind, h, w, 7000 + 64 * b + j)
+            ref = wide_reference(x, kind, wavelet, L)
+            p = dwt.Plan(w, h, wavelet, L, kind, scheme=str(rng.choice(FLOAT_SCHEMES)) if kind != "i32" else "sweldens")
+            src = buffer(ref if inverse else x, TDT[kind], pad)
+            dst = buffer(np.zeros((h, w)), TDT[kind], pad)
+            reqs.append(p.request(src, dst, inverse=inverse))
+            keep.append((src, dst))
+            plans.append(p)
+            checks.append((dst, x if inverse else ref, kind, L,
+                           f"batch {b} request {j}: h={h} w={w} L={L} {kind} {wavelet} "
+                           f"{'inv' if inverse else 'fwd'} pitch={pad}"))
+        status = torch.zeros(len(reqs), dtype=torch.int32, device="cuda")
+        dwt.submit(reqs, status=status)
+        torch.cuda.synchronize()
+        assert int(status.abs().max()) == 0
+        for dst, want, kind, L, what in checks:
+            assert_close(dst.cpu().numpy(), want, kind, L, what)
+        for p in plans:
+            p.close()
+
