@@ -7,7 +7,12 @@
  * 2-D lifting steps (Sec. 2.4-4) built from the 1-D predict/update pairs of
  * the wavelet (Sec. 2.2, Sec. 5).  Every scheme (separable, single-loop,
  * Iwahashi, Explosive, Monolithic, Polyphase, their starred variants and
- * Convolution) computes the same coefficients up to rounding (Sec. 7).
+ * Convolution) computes the same coefficients up to rounding (Sec. 7).  In
+ * float32 the rounding differs by scheme: the unstarred Polyphase with
+ * CDF 9/7 evaluates each merged step V = PU + 1 as one 2-D FIR and rounds
+ * about twice as much as the lifting schemes (about 1e-3 against 3-7e-4
+ * after one level on 8-bit samples, up to 2.2e-3 after six); DD 13/7, whose
+ * coefficients are dyadic, stays near 1e-4 in every scheme.
  *
  * Conventions shared by every entry point:
  *   - Images are row-major 2-D planes with a row pitch in BYTES (a multiple
@@ -102,11 +107,13 @@ typedef enum { DWT_NORM_JPEG2000 = 0, DWT_NORM_ZETA = 1 } dwt_norm;
  * and storage type.  Host-only: the plan's device memory (its status word
  * and one LL buffer per level after the first, each of ceil(W_k/2) x
  * ceil(H_k/2) elements with rows at a 128-byte pitch, about w*h/3 elements
- * in all) is allocated by its first single-image call, so plans used only in batches never touch
- * device memory and are cheap to create and destroy.  Errors: DWT_EINVAL for
- * w or h outside 1..2^28, levels < 0, levels above the number of halvings
- * until both dimensions are 1, or out == NULL; DWT_EUNSUPPORTED for DWT_I32 with a wavelet other
- * than 5/3 and for DWT_DD137 with a storage type other than DWT_F32; DWT_ENOMEM; DWT_ECUDA. */
+ * in all) is allocated by its first single-image call, so plans used only
+ * in batches never touch device memory and are cheap to create and
+ * destroy.  Errors: DWT_EINVAL for w or h outside 1..2^28, levels < 0,
+ * levels above the number of halvings until both dimensions are 1, or
+ * out == NULL; DWT_EUNSUPPORTED for DWT_I32 with a wavelet other than 5/3
+ * and for DWT_DD137 with a storage type other than DWT_F32; DWT_ENOMEM;
+ * DWT_ECUDA. */
 dwt_status dwt_plan_create(int w, int h, dwt_wavelet wavelet, int levels, dwt_dtype dtype,
                            dwt_plan* out);
 
@@ -239,10 +246,9 @@ dwt_status dwt2_inverse_host(dwt_plan plan, const void* h_coef, size_t coef_pitc
  * may appear in any number of requests; outputs may not overlap each other
  * or any input (DWT_EINVAL).  Batches take every plan: CDF 5/3 and 9/7 in
  * float32 and float16 storage, DD 13/7 in float32, reversible 5/3 in int32.
- * The call uploads its work list
- * from a ring of page-locked buffers and may wait for the upload of the
- * batch that last used its slot, so it cannot be captured into a CUDA
- * graph. */
+ * The call uploads its work list from a ring of page-locked buffers and may
+ * wait for the upload of the batch that last used its slot, so it cannot be
+ * captured into a CUDA graph. */
 typedef struct {
   dwt_plan plan;
   const void* in;
@@ -306,12 +312,11 @@ dwt_status dwt_plan_read_profile(dwt_plan plan, dwt_kernel_stat* stats, int capa
  * trial image (device memory allocated and freed here) for every scheme the
  * plan's wavelet and dtype support, each at its default strip height, then
  * the strip height (6..48 rows) and the ring depth (1..4 stages) for the
- * fastest scheme.  The choice applies
- * to this plan (the scheme if it is DWT_AUTO, the tile unless the caller set
- * one) and is appended to the cache file named by the environment variable
- * DWT_AUTOTUNE_CACHE (if set), which later plans of the same GPU, size,
- * wavelet, dtype and level count read.  The halo width follows from the
- * scheme and wavelet. */
+ * fastest scheme.  The choice applies to this plan (the scheme if it is
+ * DWT_AUTO, the tile unless the caller set one) and is appended to the
+ * cache file named by the environment variable DWT_AUTOTUNE_CACHE (if set),
+ * which later plans of the same GPU, size, wavelet, dtype and level count
+ * read.  The halo width follows from the scheme and wavelet. */
 dwt_status dwt_plan_autotune(dwt_plan plan, dwt_stream stream);
 
 /* Counts of the forward program a scheme runs, computed at compile time
