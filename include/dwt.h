@@ -12,7 +12,7 @@
  * CDF 9/7 evaluates each merged step V = PU + 1 as one 2-D FIR and rounds
  * about twice as much as the lifting schemes (about 1e-3 against 3-7e-4
  * after one level on 8-bit samples, up to 2.2e-3 after six); DD 13/7, whose
- * coefficients are dyadic, stays near 1e-4 in every scheme.
+ * coefficients are dyadic, stays at or below 4e-4 in every scheme.
  *
  * Conventions shared by every entry point:
  *   - Images are row-major 2-D planes with a row pitch in BYTES (a multiple

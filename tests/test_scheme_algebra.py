@@ -87,3 +87,45 @@ def test_scheme_steps_on_image_match_oracle(wname, scheme, h, w):
     assert np.abs(crop[1][:, :fw] - ref[:ch, cw:]).max() < 1e-9
     assert np.abs(crop[2][:fh, :] - ref[ch:, :cw]).max() < 1e-9
     assert np.abs(crop[3][:fh, :fw] - ref[ch:, cw:]).max() < 1e-9
+
+
+def _steps_in(dtype, name, pairs, x):
+    """The scheme's step matrices applied one by one to the quadruples of x
+    (periodic extension), every product and sum rounded to `dtype`."""
+    comps = [x[0::2, 0::2], x[0::2, 1::2], x[1::2, 0::2], x[1::2, 1::2]]
+    comps = [c.astype(dtype) for c in comps]
+    for m in sa.scheme_matrices(name, pairs):
+        out = []
+        for i in range(4):
+            acc = np.zeros(comps[0].shape, dtype)
+            for j in range(4):
+                for (ev, eh), c in sorted(m[i][j].t.items()):
+                    shifted = np.roll(np.roll(comps[j], -ev, 0), -eh, 1)
+                    acc = (acc + dtype(float(c)) * shifted).astype(dtype)
+            out.append(acc)
+        comps = out
+    return comps
+
+
+def test_float32_rounding_of_the_merged_polyphase_step():
+    """Independent of the kernels: the schemes' own step matrices evaluated
+    in float32 on 8-bit noise.  The unstarred Polyphase scheme with CDF 9/7
+    (each pair one merged 2-D step V = PU + 1) rounds more than twice as
+    much as the lifting schemes, the starred Polyphase among them; with
+    DD 13/7, whose coefficients are dyadic, every scheme stays below the
+    9/7 lifting schemes.  This is the float32 behaviour the GPU tests
+    record for the unstarred Polyphase 9/7."""
+    x = np.random.default_rng(1).integers(0, 256, (128, 128)).astype(np.float64)
+    W = wavelets()
+    err = {}
+    for wname in ("CDF 9/7", "DD 13/7"):
+        pairs = W[wname][0]
+        for name in ("Sweldens", "Iwahashi", "Explosive", "Monolithic", "Monolithic*", "Polyphase", "Polyphase*"):
+            exact = _steps_in(np.float64, name, pairs, x)
+            f32 = _steps_in(np.float32, name, pairs, x)
+            err[wname, name] = max(float(np.abs(a.astype(np.float64) - b).max()) for a, b in zip(f32, exact))
+    lifting97 = [err["CDF 9/7", s] for s in ("Sweldens", "Iwahashi", "Explosive", "Monolithic", "Monolithic*",
+                                              "Polyphase*")]
+    assert err["CDF 9/7", "Polyphase"] > 1.6 * max(lifting97), err
+    assert max(lifting97) < 1e-3 and err["CDF 9/7", "Polyphase"] < 2e-3, err
+    assert max(v for (w, _), v in err.items() if w == "DD 13/7") < 0.75 * min(lifting97), err
