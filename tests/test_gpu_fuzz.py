@@ -223,13 +223,13 @@ def wide_reference(x, kind, wavelet, L):
 
 
 # The unstarred Polyphase scheme with CDF 9/7 evaluates each merged step
-# V = PU + 1 as one 2-D FIR: about 20 float32 roundings per output and step
-# at magnitudes up to ~1000 (centre tap (1 + 2 gamma delta)^2 = 3.18 for the
-# second pair), against about 6 for a lifting pair.  Measured on 8-bit
-# noise: 1.0e-3 after one level (the lifting schemes 3-7e-4) and up to
-# 2.2e-3 after five or six levels, so it misses the 2e-3 bar by up to 10 %;
-# its own bar is 2.5e-3.  (DD 13/7, with dyadic coefficients, stays near
-# 1e-4 in every scheme.)
+# V = PU + 1 as one 2-D FIR whose rows have l1 norms up to 17.4, so the
+# float32 rounding of its inputs (the previous step's outputs, up to ~1000
+# in magnitude) is amplified far more than by a lifting step (at most
+# 1 + 2 |alpha| = 4.2).  Measured on 8-bit noise: 1.0e-3 after one level
+# (the lifting schemes 3-7e-4) and up to 2.2e-3 after five or six levels,
+# so it misses the 2e-3 bar by up to 10 %; its own bar is 2.5e-3.  (DD 13/7,
+# with dyadic coefficients, stays at or below 4e-4 in every scheme.)
 TOL_F32_POLYPHASE97 = 2.5e-3
 
 
