@@ -38,9 +38,10 @@ inline int batch_runtime_kind(int kind) {
 }
 
 // One (request, level): everything a strip of it needs.  The tensor maps
-// come first so that every element of an array of these is 64-byte aligned.
+// come first; their own alignment (that of CUtensorMap, at least the 64
+// bytes TMA requires) aligns every element of an array of these.
 // Strips are numbered row-major: strip = rs * a.ncs + cs.
-struct alignas(64) BatchLevel {
+struct BatchLevel {
   TmaMaps maps;
   LevelArgs a;
   Coefs cf;
@@ -50,6 +51,8 @@ struct alignas(64) BatchLevel {
   int dep_row_base;  // the same for the level whose output it reads, or -1
   int dep_ncs;       // column strips per row of that level: the count a row of it waits for
 };
+
+static_assert(alignof(BatchLevel) % 64 == 0, "tensor maps in a BatchLevel array must stay 64-byte aligned");
 
 struct BatchItem {
   int level;

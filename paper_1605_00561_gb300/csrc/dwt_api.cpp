@@ -987,8 +987,8 @@ dwt_status run_level(dwt_plan_s* p, bool inverse, int k, int scheme, const Lifti
   LevelArgs v = a, hz = a;
   const Coefs cv = make_coefs(L, p->norm, a.W, a.H, PASS_VERT, inverse);
   const Coefs chz = make_coefs(L, p->norm, a.W, a.H, PASS_HORZ, inverse);
-  LaunchKey kv{p->wavelet, p->dtype, DWT_ROWCOL, PASS_VERT, inverse ? 1 : 0};
-  LaunchKey kh{p->wavelet, p->dtype, DWT_ROWCOL, PASS_HORZ, inverse ? 1 : 0};
+  LaunchKey kv{p->wavelet, p->dtype, DWT_ROWCOL, PASS_VERT, inverse ? 1 : 0, 0};
+  LaunchKey kh{p->wavelet, p->dtype, DWT_ROWCOL, PASS_HORZ, inverse ? 1 : 0, 0};
   dwt_status st;
   if (!inverse) {
     v.src[0] = samples;
